@@ -1,0 +1,244 @@
+"""Seeded synthetic input instances for robust sample sort.
+
+This module only draws inputs; it holds none of the sorting method's
+arithmetic.  Both sides of every parity check (the CPU oracle and the CUDA
+library) consume the same arrays produced here.
+
+All random numbers come from the splitmix64 counter generator (Steele, Lea &
+Flood 2014): output c of the stream with state s is
+``mix(s + (c + 1) * 0x9e3779b97f4a7c15)``.  Each instance uses its own stream
+state ``splitmix64(seed, instance_id)``.
+
+The instance names follow the Helman et al. inputs that the paper runs
+(Section 6 and Appendix "Experimental Results"); where the paper's wording is
+incomplete the readings below are used (they are listed in the design doc):
+
+* partition ``i`` of ``p`` holds positions ``[floor(i*n/p), floor((i+1)*n/p))``
+  (element ``e`` is in partition ``floor(e*p/n)``);
+* "slice ``s``" of the key range is ``[s*w, (s+1)*w)`` with
+  ``w = floor((2**64 - 1) / p)``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+U64 = np.uint64
+_GAMMA = U64(0x9E3779B97F4A7C15)
+_M1 = U64(0xBF58476D1CE4E5B9)
+_M2 = U64(0x94D049BB133111EB)
+_MASK = (1 << 64) - 1
+_CHUNK = 1 << 22
+
+NAMES = ("uniform", "gaussian", "reverse", "bucket_sorted", "staggered", "g_group",
+         "mirrored", "all_to_one", "zero", "rand_dupl", "deter_dupl")
+_IDS = {name: i + 1 for i, name in enumerate(NAMES)}
+_IDS["segmented_f64"] = 101
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> U64(30))) * _M1
+        z = (z ^ (z >> U64(27))) * _M2
+    return z ^ (z >> U64(31))
+
+
+def splitmix64(state: int, counters: np.ndarray) -> np.ndarray:
+    """Vectorised splitmix64: output ``counters[i]`` of the stream at ``state``."""
+    c = np.asarray(counters, dtype=U64)
+    with np.errstate(over="ignore"):
+        z = U64(state & _MASK) + (c + U64(1)) * _GAMMA
+    return _mix(z)
+
+
+def splitmix64_scalar(state: int, counter: int) -> int:
+    z = (state + (counter + 1) * 0x9E3779B97F4A7C15) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def _stream(seed: int, name: str) -> int:
+    return splitmix64_scalar(seed & _MASK, _IDS[name])
+
+
+def _rand(state: int, lo: int, hi: int) -> np.ndarray:
+    return splitmix64(state, np.arange(lo, hi, dtype=U64))
+
+
+def _slice_width(p: int) -> int:
+    return _MASK // p
+
+
+def _partition_of(e: np.ndarray, n: int, p: int) -> np.ndarray:
+    # floor(e * p / n) without overflow for n < 2**32 and p < 2**31
+    return (e.astype(U64) * U64(p)) // U64(n)
+
+
+def _partition_start(i: np.ndarray, n: int, p: int) -> np.ndarray:
+    # first position e with floor(e*p/n) == i is ceil(i*n/p)
+    i = i.astype(U64)
+    return (i * U64(n) + U64(p - 1)) // U64(p)
+
+
+def _fill(n: int, fn) -> np.ndarray:
+    out = np.empty(n, dtype=U64)
+    for lo in range(0, n, _CHUNK):
+        hi = min(n, lo + _CHUNK)
+        out[lo:hi] = fn(lo, hi)
+    return out
+
+
+def generate(name: str, n: int, p: int = 1024, seed: int = 1, g: int = 32) -> np.ndarray:
+    """Keys (uint64) of instance ``name`` with ``n`` elements over ``p`` partitions."""
+    if name not in _IDS:
+        raise ValueError(f"unknown instance {name!r}; known: {NAMES}")
+    if n < 0 or n > 0xFFFFFFFF:
+        raise ValueError("n must be in [0, 2**32 - 1]")
+    if n == 0:
+        return np.empty(0, dtype=U64)
+    st = _stream(seed, name)
+    w = _slice_width(p)
+
+    if name == "uniform":
+        return _fill(n, lambda lo, hi: _rand(st, lo, hi))
+
+    if name == "gaussian":
+        # round(2**63 + 2**60 * z), z ~ N(0, 1) by Box-Muller, clamped to [0, 2**64 - 1]
+        def gauss(lo, hi):
+            r1 = splitmix64(st, 2 * np.arange(lo, hi, dtype=U64))
+            r2 = splitmix64(st, 2 * np.arange(lo, hi, dtype=U64) + U64(1))
+            u1 = ((r1 >> U64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+            u2 = (r2 >> U64(11)).astype(np.float64) * 2.0 ** -53
+            z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+            v = np.rint(2.0 ** 63 + 2.0 ** 60 * z)
+            out = np.empty(hi - lo, dtype=U64)
+            big = v >= 2.0 ** 64
+            neg = v <= 0.0
+            mid = ~(big | neg)
+            out[mid] = v[mid].astype(U64)
+            out[big] = U64(_MASK)
+            out[neg] = U64(0)
+            return out
+        return _fill(n, gauss)
+
+    if name == "reverse":
+        # strictly descending: slot n-1-i of width floor((2**64-1)/n), random inside
+        ws = _MASK // n
+
+        def rev(lo, hi):
+            e = np.arange(lo, hi, dtype=U64)
+            r = _rand(st, lo, hi) % U64(ws)
+            with np.errstate(over="ignore"):
+                return (U64(n - 1) - e) * U64(ws) + r
+        return _fill(n, rev)
+
+    if name in ("bucket_sorted", "staggered", "all_to_one"):
+        def sliced(lo, hi):
+            e = np.arange(lo, hi, dtype=U64)
+            part = _partition_of(e, n, p)
+            if name == "bucket_sorted":
+                sl = part
+            elif name == "staggered":
+                half = U64(p // 2)
+                sl = np.where(part < half, U64(2) * part + U64(1), U64(2) * (part - half))
+            else:
+                sl = np.zeros_like(part)
+            with np.errstate(over="ignore"):
+                return sl * U64(w) + _rand(st, lo, hi) % U64(w)
+        return _fill(n, sliced)
+
+    if name == "g_group":
+        def grouped(lo, hi):
+            e = np.arange(lo, hi, dtype=U64)
+            part = _partition_of(e, n, p)
+            local = e - _partition_start(part, n, p)
+            grp = part // U64(g)
+            sl = (grp * U64(g) + U64(p // 2) + local % U64(g)) % U64(p)
+            with np.errstate(over="ignore"):
+                return sl * U64(w) + _rand(st, lo, hi) % U64(w)
+        return _fill(n, grouped)
+
+    if name == "mirrored":
+        # first ceil(n/2) uniform, a[n-1-j] = a[j]
+        out = np.empty(n, dtype=U64)
+        first = n - n // 2
+        out[:first] = _fill(first, lambda lo, hi: _rand(st, lo, hi))
+        if n // 2:
+            out[first:] = out[: n // 2][::-1]
+        return out
+
+    if name == "zero":
+        return np.zeros(n, dtype=U64)
+
+    if name == "rand_dupl":
+        # runs of length uniform in [1, 4096], each run one value uniform in {0..15}
+        lengths = []
+        values = []
+        total = 0
+        r = 0
+        while total < n:
+            batch = max(16, (n - total) // 2048 + 16)
+            rl = splitmix64(st, 2 * np.arange(r, r + batch, dtype=U64))
+            rv = splitmix64(st, 2 * np.arange(r, r + batch, dtype=U64) + U64(1))
+            lengths.append((rl % U64(4096) + U64(1)).astype(np.int64))
+            values.append(rv % U64(16))
+            total += int(lengths[-1].sum())
+            r += batch
+        return np.repeat(np.concatenate(values), np.concatenate(lengths))[:n].astype(U64)
+
+    if name == "deter_dupl":
+        def dd(lo, hi):
+            v = _partition_of(np.arange(lo, hi, dtype=U64), n, p) + U64(1)
+            lg = np.zeros(hi - lo, dtype=U64)
+            for b in range(1, 64):
+                lg += (v >> U64(b)) > 0
+            return lg
+        return _fill(n, dd)
+
+    raise AssertionError(name)
+
+
+def segmented_f64(num_segments: int, max_log2: int, seed: int = 1, dup_frac: float = 0.1,
+                  total_cap: int | None = None):
+    """Batched segmented instance: float64 N(0, 1) keys (as raw uint64 bits).
+
+    Segment sizes are floor(exp(U * ln(2**max_log2))) with U uniform in [0, 1),
+    i.e. log-uniform in [1, 2**max_log2).  Roughly ``dup_frac`` of the positions
+    of every segment are overwritten by a copy of another key of the same
+    segment (exact duplicates).  ``total_cap`` stops drawing segments once the
+    total would pass it.  Returns ``(keys_bits, offsets)``.
+    """
+    st = _stream(seed, "segmented_f64")
+    ru = splitmix64(st, np.arange(num_segments, dtype=U64))
+    u = (ru >> U64(11)).astype(np.float64) * 2.0 ** -53
+    sizes = np.floor(np.exp(u * (max_log2 * math.log(2.0)))).astype(np.int64)
+    sizes = np.clip(sizes, 1, (1 << max_log2))
+    if total_cap is not None:
+        cum = np.cumsum(sizes)
+        sizes = sizes[cum <= total_cap]
+    offsets = np.zeros(sizes.shape[0] + 1, dtype=U64)
+    offsets[1:] = np.cumsum(sizes).astype(U64)
+    n = int(offsets[-1])
+    base = U64(num_segments) * U64(4)
+    keys = np.empty(n, dtype=np.float64)
+    for lo in range(0, n, _CHUNK):
+        hi = min(n, lo + _CHUNK)
+        e = np.arange(lo, hi, dtype=U64)
+        r1 = splitmix64(st, base + U64(4) * e)
+        r2 = splitmix64(st, base + U64(4) * e + U64(1))
+        u1 = ((r1 >> U64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        u2 = (r2 >> U64(11)).astype(np.float64) * 2.0 ** -53
+        keys[lo:hi] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    if dup_frac > 0 and n:
+        seg_of = np.repeat(np.arange(sizes.shape[0]), sizes)
+        starts = offsets[:-1].astype(np.int64)
+        e = np.arange(n, dtype=U64)
+        rsel = splitmix64(st, base + U64(4) * e + U64(2))
+        rsrc = splitmix64(st, base + U64(4) * e + U64(3))
+        pick = (rsel >> U64(11)).astype(np.float64) * 2.0 ** -53 < dup_frac
+        src = starts[seg_of] + (rsrc % sizes[seg_of].astype(U64)).astype(np.int64)
+        idx = np.nonzero(pick)[0]
+        keys[idx] = keys[src[idx]]
+    return keys.view(U64), offsets

@@ -1,0 +1,295 @@
+/*
+ * oracle.c -- plain, slow, obviously correct CPU oracle for robust sample sort.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file.  Only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference leg of bench.py may load it.  It shares no code, header, table or
+ * constant generator with the CUDA path: every definition below is written out
+ * again here from the paper (Axtmann & Sanders, "Robust Massively Parallel
+ * Sorting", arXiv 1606.08766).
+ *
+ * What it computes
+ *   oracle_sort        The output contract of Section 2 ("Preliminaries"): the
+ *                      globally sorted sequence.  Ties are broken by the
+ *                      original position, the "append a unique identifier and
+ *                      compare lexicographically" semantics of Section 2 that
+ *                      the robust algorithms simulate implicitly (Section 5,
+ *                      Appendix "Robust Multi-Level Sample Sort").  Because
+ *                      positions are distinct the result is unique:
+ *                      perm is the permutation with (phi(x[perm[j]]), perm[j])
+ *                      strictly increasing in j.  Textbook top-down merge sort.
+ *   oracle_segmented   The same contract applied to each segment on its own
+ *                      (segment-local positions).
+ *   oracle_partition   One level of the robust sample-sort partition step
+ *                      (Appendix "Robust Multi-Level Sample Sort"), step by
+ *                      step in the paper's order: draw samples and attach their
+ *                      input positions as tie-breakers, rank (sort) the sample,
+ *                      take every S/k-th sample as a splitter (Appendix
+ *                      "Generalizing Quicksort"), assign every element to the
+ *                      partition given by the number of splitters that are
+ *                      lexicographically smaller than (key, position), and lay
+ *                      the partitions out in order.
+ *
+ * Readings where the paper is silent (each also listed in the design doc):
+ *   - phi: 64-bit floating-point elements (Appendix "Experimental Results") are
+ *     ordered by their IEEE-754 bit pattern mapped to an unsigned integer
+ *     (negative: all bits flipped; non-negative: sign bit flipped), so
+ *     -0.0 < +0.0.  Unsigned 64-bit keys use the identity.
+ *   - sample size S = min(n, a*k) with a = 16 * ceil(log2 k) samples per
+ *     partition (the 16 log p samples per PE of Appendix "Implementation
+ *     Details").
+ *   - sampling: stratified, sample j drawn from positions
+ *     [floor(j*n/S), floor((j+1)*n/S)) at offset h(seed, j) mod (stratum
+ *     size), with h the splitmix64 generator
+ *     (Steele, Lea & Flood 2014): h(s, j) = mix(s + (j+1) * 0x9e3779b97f4a7c15).
+ *   - splitter j (j = 1..k-1) is the sorted sample's element floor(j*S/k).
+ *
+ * parity pins: see tests/test_oracle_pins.py.  All functions are pinned.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------- */
+/* Key order                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Order-preserving map of the raw 64-bit pattern to an unsigned key.
+ * key_type 0: unsigned 64-bit integer, identity.
+ * key_type 1: IEEE-754 binary64: flip every bit of a negative pattern, flip
+ *             only the sign bit of a non-negative one. */
+static uint64_t phi(uint64_t bits, int key_type)
+{
+    if (key_type == 0)
+        return bits;
+    if (bits >> 63)                 /* sign bit set: negative number */
+        return ~bits;
+    return bits | 0x8000000000000000ULL;
+}
+
+/* Lexicographic order on (key, position): the unique-identifier order of
+ * Section 2. */
+static int pair_less(uint64_t ka, uint64_t pa, uint64_t kb, uint64_t pb)
+{
+    if (ka != kb)
+        return ka < kb;
+    return pa < pb;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Textbook top-down merge sort of an index array                           */
+/* ---------------------------------------------------------------------- */
+
+/* Sorts idx[lo, hi) by (key[idx], idx); scratch has the same extent. */
+static void merge_sort(uint32_t *idx, uint32_t *scratch, uint64_t lo, uint64_t hi,
+                       const uint64_t *key)
+{
+    if (hi - lo < 2)
+        return;
+    uint64_t mid = lo + (hi - lo) / 2;
+    merge_sort(idx, scratch, lo, mid, key);
+    merge_sort(idx, scratch, mid, hi, key);
+    /* merge the two sorted halves into scratch, then copy back */
+    uint64_t i = lo, j = mid, o = lo;
+    while (i < mid && j < hi) {
+        uint32_t a = idx[i], b = idx[j];
+        if (pair_less(key[b], b, key[a], a))
+            scratch[o++] = idx[j++];
+        else
+            scratch[o++] = idx[i++];
+    }
+    while (i < mid)
+        scratch[o++] = idx[i++];
+    while (j < hi)
+        scratch[o++] = idx[j++];
+    memcpy(idx + lo, scratch + lo, (size_t)(hi - lo) * sizeof(uint32_t));
+}
+
+/* Sorted output contract of Section 2 with position tie-breaking.
+ * keys_bits: n raw 64-bit patterns.  Writes keys_out[j] = keys_bits[perm[j]]
+ * and perm_out.  Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_sort(const uint64_t *keys_bits, uint64_t n, int key_type,
+                uint64_t *keys_out, uint32_t *perm_out)
+{
+    if (n > 0xFFFFFFFFULL || (key_type != 0 && key_type != 1))
+        return -1;
+    if (n == 0)
+        return 0;
+    uint64_t *key = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint32_t *scratch = (uint32_t *)malloc(n * sizeof(uint32_t));
+    if (!key || !scratch) {
+        free(key);
+        free(scratch);
+        return -1;
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+        key[i] = phi(keys_bits[i], key_type);
+        perm_out[i] = (uint32_t)i;
+    }
+    merge_sort(perm_out, scratch, 0, n, key);
+    for (uint64_t j = 0; j < n; ++j)
+        keys_out[j] = keys_bits[perm_out[j]];
+    free(key);
+    free(scratch);
+    return 0;
+}
+
+/* The same contract applied to every segment [offsets[s], offsets[s+1]) on its
+ * own; perm_out holds segment-local positions. */
+int oracle_segmented(const uint64_t *keys_bits, const uint64_t *offsets, uint32_t nseg,
+                     int key_type, uint64_t *keys_out, uint32_t *perm_out)
+{
+    for (uint32_t s = 0; s < nseg; ++s) {
+        uint64_t a = offsets[s], b = offsets[s + 1];
+        if (b < a)
+            return -1;
+        int rc = oracle_sort(keys_bits + a, b - a, key_type, keys_out + a, perm_out + a);
+        if (rc)
+            return rc;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* splitmix64 (Steele, Lea & Flood 2014), counter form                      */
+/* ---------------------------------------------------------------------- */
+
+/* Output number c (0-based) of the splitmix64 stream whose state starts at s:
+ * the state advances by the golden gamma before each output, and the output is
+ * the state passed through the two xor-shift-multiply rounds and a final
+ * xor-shift. */
+uint64_t oracle_splitmix64_at(uint64_t s, uint64_t c)
+{
+    uint64_t z = s + (c + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* ---------------------------------------------------------------------- */
+/* One level of the robust sample-sort partition step                       */
+/* ---------------------------------------------------------------------- */
+
+static uint32_t ceil_log2_u32(uint32_t k)
+{
+    uint32_t l = 0;
+    while ((1ULL << l) < k)
+        ++l;
+    return l;
+}
+
+/* Number of samples drawn for n elements and k partitions. */
+uint64_t oracle_sample_count(uint64_t n, uint32_t k)
+{
+    uint64_t a = 16ULL * ceil_log2_u32(k);
+    uint64_t s = a * k;
+    return s < n ? s : n;
+}
+
+/* Partitions n keys into k >= 1 buckets (Appendix "Robust Multi-Level Sample
+ * Sort").  Outputs (each may be NULL except where noted):
+ *   sample_pos  [S]    the sampled input positions, in draw order
+ *   spl_key     [k-1]  splitter keys (mapped by phi), spl_pos [k-1] positions
+ *   bucket      [n]    partition of every input element
+ *   keys_out    [n]    raw key bits laid out partition by partition, each
+ *   pos_out     [n]    partition in increasing input position
+ *   offsets     [k+1]  start of every partition; offsets[k] = n
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_partition(const uint64_t *keys_bits, uint64_t n, int key_type, uint32_t k,
+                     uint64_t seed, uint64_t *sample_pos, uint64_t *spl_key,
+                     uint32_t *spl_pos, uint32_t *bucket, uint64_t *keys_out,
+                     uint32_t *pos_out, uint64_t *offsets)
+{
+    if (k == 0 || n > 0xFFFFFFFFULL || (key_type != 0 && key_type != 1))
+        return -1;
+    uint64_t S = oracle_sample_count(n, k);
+    uint64_t *key = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint32_t *b = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    uint64_t *skey = (uint64_t *)malloc((S ? S : 1) * sizeof(uint64_t));
+    uint32_t *sidx = (uint32_t *)malloc((S ? S : 1) * sizeof(uint32_t));
+    uint32_t *sscr = (uint32_t *)malloc((S ? S : 1) * sizeof(uint32_t));
+    uint64_t *tk = (uint64_t *)malloc((k ? k : 1) * sizeof(uint64_t));
+    uint32_t *ti = (uint32_t *)malloc((k ? k : 1) * sizeof(uint32_t));
+    uint64_t *cnt = (uint64_t *)calloc((size_t)k + 1, sizeof(uint64_t));
+    int rc = -1;
+    if (!key || !b || !skey || !sidx || !sscr || !tk || !ti || !cnt)
+        goto done;
+    for (uint64_t i = 0; i < n; ++i)
+        key[i] = phi(keys_bits[i], key_type);
+
+    /* Step 1: random samples of the data, each carrying its input position as
+     * tie-breaker.  Stratified: sample j comes from stratum
+     * [floor(j*n/S), floor((j+1)*n/S)), so the strata tile the whole input. */
+    uint32_t *sample_order = sidx; /* sample number -> input position */
+    if (S > 0) {
+        for (uint64_t j = 0; j < S; ++j) {
+            uint64_t lo = (j * n) / S, hi = ((j + 1) * n) / S;
+            uint64_t pos = lo + oracle_splitmix64_at(seed, j) % (hi - lo);
+            sample_order[j] = (uint32_t)pos;
+            if (sample_pos)
+                sample_pos[j] = pos;
+        }
+    }
+
+    /* Step 2: rank the samples by (key, position): sort the sample positions
+     * with the same textbook merge sort (the key array is indexed by input
+     * position, so sorting positions sorts the pairs). */
+    merge_sort(sample_order, sscr, 0, S, key);
+    for (uint64_t j = 0; j < S; ++j)
+        skey[j] = key[sample_order[j]];
+
+    /* Step 3: every S/k-th sample becomes a splitter: splitter j (1-based,
+     * j = 1..k-1) is sorted sample floor(j*S/k).  With S = 0 there are no
+     * elements and no splitters are needed. */
+    for (uint32_t j = 1; j < k && S > 0; ++j) {
+        uint64_t r = ((uint64_t)j * S) / k;
+        tk[j - 1] = skey[r];
+        ti[j - 1] = sample_order[r];
+        if (spl_key)
+            spl_key[j - 1] = skey[r];
+        if (spl_pos)
+            spl_pos[j - 1] = sample_order[r];
+    }
+
+    /* Step 4: classify.  An element (x, i) goes to partition
+     * b = #{ splitters (s.key, s.pos) lexicographically smaller than (x, i) }:
+     * the search on the key alone, repeated with positions as tie-breakers when
+     * the key equals the bounding splitter's key, counts exactly these. */
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t c = 0;
+        for (uint32_t j = 0; j + 1 < k; ++j)
+            if (pair_less(tk[j], ti[j], key[i], i))
+                ++c;
+        b[i] = c;
+        if (bucket)
+            bucket[i] = c;
+        cnt[c + 1] += 1;
+    }
+
+    /* Step 5: lay the partitions out in order, each in increasing position. */
+    for (uint32_t j = 0; j < k; ++j)
+        cnt[j + 1] += cnt[j];
+    if (offsets)
+        for (uint32_t j = 0; j <= k; ++j)
+            offsets[j] = cnt[j];
+    if (keys_out || pos_out) {
+        for (uint64_t i = 0; i < n; ++i) {
+            uint64_t o = cnt[b[i]]++;
+            if (keys_out)
+                keys_out[o] = keys_bits[i];
+            if (pos_out)
+                pos_out[o] = (uint32_t)i;
+        }
+    }
+    rc = 0;
+done:
+    free(key);
+    free(b);
+    free(skey);
+    free(sidx);
+    free(sscr);
+    free(tk);
+    free(ti);
+    free(cnt);
+    return rc;
+}
