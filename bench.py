@@ -1,0 +1,316 @@
+"""Benchmark: robust sample sort of 2^28 uint64 keys (p = 1024 virtual
+partitions, Uniform instance, seed 1) on one GB300, through the C ABI.
+
+Prints ONE JSON line (rank 0).  A step is one full rsort_sort call (all
+partition levels and the in-SM bucket sorts) over the resident input.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsort|reference]
+
+--impl reference times the CPU oracle (a textbook merge sort on (key,
+position)) on the host cores, on bounded samples of the same workload.
+With N > 1 (torchrun) every rank sorts its own instance (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_KEYS = 1 << 28
+P_VIRTUAL = 1024
+WORKLOAD = "Uniform uint64 keys, n=2^28, p=1024 virtual partitions, seed 1"
+METRIC = "GKeys/s"
+CPU_SAMPLE = 1 << 24
+
+# algorithmic HBM bytes per key of each kernel's input (8 B key, 4 B position)
+ALGO_BYTES_PER_KEY = {
+    "L1.classify": 8,       # read keys
+    "L1.scatter": 20,       # read keys, write (key, position)
+    "L2.classify": 8,       # read keys (positions only on key ties)
+    "L2.scatter": 24,       # read + write (key, position)
+    "L3.classify": 8,
+    "L3.scatter": 24,
+    "local_sort": 24,       # read + write (key, position)
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on bounded samples of the same workload."""
+    import numpy as np
+
+    import instances
+    import oracle
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    keys = instances.generate("uniform", N_KEYS, p=P_VIRTUAL, seed=1)
+    times = []
+    for step in range(args.warmup + args.steps):
+        lo = (step * CPU_SAMPLE) % (N_KEYS - CPU_SAMPLE)
+        sample = np.ascontiguousarray(keys[lo:lo + CPU_SAMPLE])
+        t0 = time.perf_counter()
+        oracle.sort(sample)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = CPU_SAMPLE / (ms / 1e3) / 1e9
+    sample_desc = f"{CPU_SAMPLE} consecutive keys of the 2^28 Uniform input per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_KEYS, "p": P_VIRTUAL},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline_leg():
+    """Oracle timed on the host on a bounded sample (rank 0, N = 1 only)."""
+    import numpy as np
+
+    import instances
+    import oracle
+
+    sample = instances.generate("uniform", CPU_SAMPLE, p=P_VIRTUAL, seed=1)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.sort(np.ascontiguousarray(sample))
+        ts.append(time.perf_counter() - t0)
+    v = CPU_SAMPLE / statistics.median(ts) / 1e9
+    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE} keys of the Uniform instance, 3 runs, median"}
+
+
+def run_rsort(args):
+    import numpy as np
+    import torch
+
+    import instances
+    from paper_1606_08766_gb300 import Context
+
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = N_KEYS
+    keys_h = instances.generate("uniform", n, p=P_VIRTUAL, seed=1 + rank)
+    keys = torch.from_numpy(keys_h.view(np.int64)).to(dev)
+    keys_out = torch.empty_like(keys)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    def step():
+        ctx.sort_raw(0, keys.data_ptr(), keys_out.data_ptr(), perm.data_ptr(), n, P_VIRTUAL,
+                     1, sh)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.check()
+
+    # -- timed region: device time with CUDA events; per-kernel events inside
+    ctx.set_profiling(True)
+    ctx.phase_times()
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    phases = ctx.phase_times()
+    ctx.set_profiling(False)
+    ctx.check()
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = (n * ws) / (ms_step / 1e3) / 1e9
+
+    # -- per-kernel roofline (dominant kernel)
+    _, _, st = ctx.sort(keys, p=P_VIRTUAL, seed=1, keys_out=keys_out, perm_out=perm, stats=True)
+    torch.cuda.synchronize(dev)
+    elems = {"L1": n, "L2": st.level_elems[1] if len(st.level_elems) > 1 else n,
+             "L3": st.level_elems[2] if len(st.level_elems) > 2 else 0, "local": n}
+    peak, peak_kind = _peaks()
+    kernels = {}
+    for name, (ms, cnt) in phases.items():
+        per = ms / max(cnt, 1)
+        info = {"ms_per_launch": per, "launches": cnt, "share": ms / max(ms_total, 1e-9)}
+        if name in ALGO_BYTES_PER_KEY:
+            lvl = name.split(".")[0] if "." in name else "local"
+            units = elems.get(lvl, n)
+            info["algo_bytes"] = ALGO_BYTES_PER_KEY[name] * units
+            info["gbs"] = info["algo_bytes"] / (per / 1e3) / 1e9
+        kernels[name] = info
+    dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["ms_per_launch"]
+              * kernels[k]["launches"])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak,
+            "unit": "GB/s", "frac": kernels[dom]["gbs"] / peak, "peak_kind": peak_kind,
+            "traffic": None}
+
+    # -- end-to-end through the C ABI with host buffers (pinned), copies timed
+    keys_pin = torch.from_numpy(keys_h.view(np.int64)).pin_memory()
+    out_pin = torch.empty(n, dtype=torch.int64).pin_memory()
+    perm_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        keys.copy_(keys_pin, non_blocking=True)
+        step()
+        out_pin.copy_(keys_out, non_blocking=True)
+        perm_pin.copy_(perm, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": (n * ws) / (e2e_ms / 1e3) / 1e9, "unit": METRIC,
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + n * 4}
+
+    cpu = cpu_baseline_leg() if (rank == 0 and ws == 1) else None
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "p": P_VIRTUAL,
+                       "l2": "inputs (2 GiB keys) larger than L2 (129 MB); no flush needed",
+                       "max_over_mean": st.max_over_mean, "levels": st.levels},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches, "kernels": kernels,
+        }))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsort", choices=["rsort", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_rsort(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,135 @@
+/*
+ * rsort.h -- C ABI of librsort, a single-GPU (GB300, sm_103a) implementation of
+ * the robust sample-sort partition step of Axtmann & Sanders, "Robust Massively
+ * Parallel Sorting" (arXiv 1606.08766), and the sorts built on it.
+ *
+ * The paper's processing elements become virtual partitions of one GPU's HBM:
+ * virtual partition i of p holds the positions [floor(i*n/p), floor((i+1)*n/p))
+ * of the input and, after partitioning, the i-th bucket of the output.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an rsort_status and never throws or aborts.
+ *   - "d_" pointers are DEVICE pointers on the context's device; the caller owns
+ *     them.  Host pointers are named without the prefix.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it and the call returns without waiting, unless the
+ *     function says otherwise.
+ *   - Keys are 64-bit patterns: RSORT_KEY_U64 orders them as unsigned
+ *     integers; RSORT_KEY_F64 orders IEEE-754 binary64 values by their bit
+ *     pattern mapped to an unsigned integer (negative: all bits flipped,
+ *     non-negative: sign bit flipped), so -0.0 < +0.0 and NaNs sit beyond the
+ *     infinities of their sign.  Outputs always hold the original bits.
+ *   - Ties are broken by the original position (Section 2: unique identifiers
+ *     compared lexicographically), so every result below is unique: it does not
+ *     depend on the seed, the plan, the batch or the device schedule.
+ *   - n <= 2^32 - 1 (positions are 32-bit); larger n gives RSORT_EINVAL.
+ *   - Errors raised asynchronously on the device (a capacity check, an expired
+ *     bounded wait) are latched in the context and returned by rsort_check(),
+ *     by a stats read-back, and by the next call.
+ */
+#ifndef RSORT_H
+#define RSORT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rsort_status;
+#define RSORT_OK 0
+#define RSORT_PENDING 1
+#define RSORT_EINVAL (-1)
+#define RSORT_ENOMEM (-2)
+#define RSORT_ECUDA (-3)
+#define RSORT_ETIMEOUT (-4)
+#define RSORT_ECANCELLED (-5)
+#define RSORT_EUNSUPPORTED (-6)
+#define RSORT_EDEVICE (-7)
+
+typedef int32_t rsort_key_type;
+#define RSORT_KEY_U64 0
+#define RSORT_KEY_F64 1
+
+typedef struct rsort_ctx rsort_ctx;
+
+/* Statistics of one rsort_sort call (read back on request). */
+typedef struct {
+    uint64_t n;              /* elements sorted                                  */
+    uint32_t p;              /* virtual partitions = level-1 buckets             */
+    uint32_t levels;         /* partition levels that had work                   */
+    uint32_t path;           /* 0: direct in-SM sort, 1: sample-sort levels       */
+    uint32_t max_bucket;     /* largest level-1 bucket (virtual partition)       */
+    double max_over_mean;    /* max_bucket / (n/p): the imbalance of Section 2    */
+    uint64_t final_buckets;  /* buckets handed to the in-SM sort                 */
+    uint64_t bytes_moved;    /* algorithmic HBM bytes of the whole call          */
+    uint64_t level_elems[4]; /* elements partitioned at levels 1..4 (0: unused)  */
+} rsort_stats;
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the scratch
+ * the context may hold (0 = no cap).  tune_table_path: NULL for the built-in
+ * plan table, else a text file of "name value" lines overriding tunables.
+ * The context owns its scratch pool; the caller owns *out and must call
+ * rsort_destroy.  Errors: EINVAL (bad device / unreadable table), ECUDA. */
+rsort_status rsort_create(rsort_ctx **out, int device, uint64_t hbm_budget_bytes,
+                          const char *tune_table_path);
+
+/* Waits for the context's outstanding work, frees its scratch and the
+ * context.  NULL is accepted and ignored. */
+rsort_status rsort_destroy(rsort_ctx *ctx);
+
+/* Static, human-readable text for a status code. */
+const char *rsort_strerror(rsort_status status);
+
+/* Synchronises the context's last stream and returns the first latched device
+ * or CUDA error (RSORT_OK if none), clearing it. */
+rsort_status rsort_check(rsort_ctx *ctx);
+
+/* ONE level of the robust sample-sort partition step (Appendix "Robust
+ * Multi-Level Sample Sort"; splitters every S/k-th sample, Appendix
+ * "Generalizing Quicksort"):
+ *   1. S = min(n, 16*ceil(log2 k)*k) samples, sample j drawn from positions
+ *      [floor(j*n/S), floor((j+1)*n/S)) at offset splitmix64(seed, j) modulo
+ *      the stratum size, each carrying its position as tie-breaker;
+ *   2. the sample is sorted by (key, position);
+ *   3. splitter j (j = 1..k-1) is sorted sample floor(j*S/k);
+ *   4. element (x, i) goes to bucket #{splitters lexicographically < (x, i)};
+ *   5. buckets are written in order, each in increasing position.
+ * d_keys_in [n] (read only, must not alias the outputs), d_keys_out [n],
+ * d_pos_out [n] (original positions), d_offsets_out [k+1] (bucket starts,
+ * d_offsets_out[k] = n).  1 <= k <= 2048.  Errors: EINVAL, ENOMEM, ECUDA. */
+rsort_status rsort_partition(rsort_ctx *ctx, rsort_key_type type, const void *d_keys_in,
+                             uint64_t n, uint32_t k, uint64_t seed, void *d_keys_out,
+                             uint32_t *d_pos_out, uint64_t *d_offsets_out, void *stream);
+
+/* Plain sort (Section 2's output contract): keys_out[j] = keys_in[perm[j]] with
+ * (key, perm[j]) strictly increasing.  Large inputs run the multi-level robust
+ * sample sort (level 1 with k = p_virtual buckets, deeper levels until buckets
+ * fit one SM, then an in-shared-memory sort per bucket: rank-by-counting for
+ * tiny buckets, bitonic for medium ones -- the paper's size-dependent choice,
+ * Section 6 and Appendix "Parameter Tuning").  d_keys_in may alias d_keys_out.
+ * p_virtual: 1 (choose automatically) or 2..2048.  seed: sampling seed (does
+ * not change the result).  opt_stats: NULL, or a host struct filled after a
+ * synchronising read-back.  Errors: EINVAL, ENOMEM, ECUDA, EDEVICE. */
+rsort_status rsort_sort(rsort_ctx *ctx, rsort_key_type type, const void *d_keys_in,
+                        void *d_keys_out, uint32_t *d_perm_out, uint64_t n,
+                        uint32_t p_virtual, uint64_t seed, void *stream,
+                        rsort_stats *opt_stats);
+
+/* Profiling (tracing): when enabled, the library records CUDA events around
+ * every kernel it launches on the call's stream.  rsort_phase_times copies up
+ * to max entries of {kernel name, accumulated milliseconds, launches} into the
+ * caller's arrays (names are static strings) after synchronising, and resets
+ * the accumulators.  *count receives the number of distinct kernels. */
+rsort_status rsort_set_profiling(rsort_ctx *ctx, int enable);
+rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
+                               uint64_t *launches, int max, int *count);
+
+/* Number of kernels this context has launched since creation. */
+rsort_status rsort_launch_count(rsort_ctx *ctx, uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSORT_H */

@@ -1,0 +1,770 @@
+// partition_kernels.cu -- one level of the robust multi-level sample sort
+// (Appendix "Robust Multi-Level Sample Sort" of Axtmann & Sanders,
+// arXiv 1606.08766) over a device-resident list of segments:
+//
+//   plan -> sample -> sort the sample -> classify + per-chunk histograms ->
+//   exclusive scan -> stable scatter -> collect the buckets
+//
+// Every segment of the level is partitioned independently; all segments share
+// the launches, so one level of a plain sort (one segment) and of a batched
+// segmented sort (thousands of segments) run the same kernels.  The paper's
+// processing elements are virtual partitions of HBM: the k buckets of a
+// segment are its k virtual partitions, and the MPI_Alltoallv data exchange of
+// the paper's sample sort becomes the scan + scatter through HBM.
+#include <cstdio>
+
+#include "rsort_internal.cuh"
+
+namespace rsort {
+
+namespace {
+
+struct Scope {
+  const LaunchEnv& e;
+  Scope(const LaunchEnv& env, const char* name) : e(env) {
+    if (e.timer) e.timer->begin(name, e.stream);
+  }
+  ~Scope() {
+    if (e.timer) e.timer->end(e.stream);
+    if (e.launches) ++*e.launches;
+  }
+};
+
+// Index of the last segment whose field is <= x (segments sorted by field).
+template <typename F>
+__device__ __forceinline__ uint32_t find_seg(const LevelSeg* segs, uint32_t G, uint64_t x,
+                                             F field) {
+  uint32_t lo = 0, hi = G;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (field(segs[mid]) <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+__device__ __forceinline__ uint32_t ceil_log2_dev(uint32_t k) {
+  uint32_t l = 0;
+  while ((1u << l) < k) ++l;
+  return l;
+}
+
+__device__ __forceinline__ uint64_t load_key(const Src& s, uint64_t pos) {
+  const uint64_t k = __ldg(s.key + pos);
+  return s.map_f64 ? f64_to_ordered(k) : k;
+}
+
+// ---------------------------------------------------------------------------
+// Splitter structures in shared memory
+//
+// The k-1 splitters of a segment are the sorted sample's elements
+// floor(j*S/k), j = 1..k-1 (Appendix "Generalizing Quicksort": every S/k-th
+// sample), kept as (key, position) pairs.  Their keys are also laid out as an
+// implicit binary search tree (Eytzinger order, padded with UINT64_MAX to
+// Kp - 1 = next_pow2(k) - 1 nodes): the branchless classifier of Super Scalar
+// Sample Sort that the appendix names.
+// ---------------------------------------------------------------------------
+struct Splitters {
+  uint64_t* tree;   // [Kp]   node i at tree[i], i = 1..Kp-1
+  uint64_t* key;    // [k-1]  sorted splitter keys
+  uint32_t* idx;    // [k-1]  their positions (tie-breakers)
+  int logK;         // log2(Kp)
+  uint32_t nspl;    // k - 1
+};
+
+template <int NT>
+__device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const uint32_t* ssi,
+                               Splitters& sp) {
+  const uint32_t k = sg.k;
+  const uint32_t Kp = next_pow2_u32(k);
+  sp.nspl = k - 1;
+  sp.logK = log2_u32(Kp);
+  for (uint32_t j = threadIdx.x; j < sp.nspl; j += NT) {
+    const uint64_t r = ((uint64_t)(j + 1) * sg.S) / k;
+    sp.key[j] = ssk[sg.samp_off + r];
+    sp.idx[j] = ssi[sg.samp_off + r];
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x + 1; i < Kp; i += NT) {
+    const int d = 31 - __clz(i);
+    const uint32_t r = i - (1u << d);
+    const uint32_t in = ((2 * r + 1) << (sp.logK - 1 - d)) - 1;
+    sp.tree[i] = in < sp.nspl ? sp.key[in] : ~0ULL;
+  }
+  __syncthreads();
+}
+
+// Bucket of element (x, i): the number of splitters lexicographically smaller
+// than (x, i).  The tree descent counts the splitters whose key is smaller
+// than x; if x equals the key of the bounding splitter, the search is repeated
+// on the run of equal splitter keys with positions as tie-breakers.
+template <typename PosFn>
+__device__ __forceinline__ uint32_t classify(uint64_t x, PosFn pos_of, const Splitters& sp) {
+  uint32_t j = 1;
+  for (int l = 0; l < sp.logK; ++l) j = 2 * j + (x > sp.tree[j] ? 1u : 0u);
+  uint32_t b = j - (1u << sp.logK);
+  if (b < sp.nspl && sp.key[b] == x) {
+    // the key equals the bounding splitter's key: break the tie by position
+    const uint32_t i = pos_of();
+    uint32_t lo = b, hi = sp.nspl;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (sp.key[mid] == x && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    b = lo;
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uint64_t n,
+                             uint32_t k1, int direct) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->nseg[0] = st->nseg[1] = 0;
+  st->nfinal = 0;
+  st->final_cursor = 0;
+  st->error = 0;
+  st->max_bucket_l1 = 0;
+  st->levels_used = 0;
+  st->cur_nseg = 0;
+  st->total_samples = st->total_chunks = st->total_hist = 0;
+  st->total_schunks = st->total_buckets = 0;
+  st->big_items = 0;
+  for (int i = 0; i < 4; ++i) st->level_elems[i] = 0;
+  if (n == 0) return;
+  if (direct) {
+    FinalItem f;
+    f.start = 0;
+    f.idx_base = 0;
+    f.size = (uint32_t)n;
+    f.where = kWhereInput;
+    f.kind = n == 1 ? kKindCopy : kKindSort;
+    items[0] = f;
+    st->nfinal = 1;
+  } else {
+    SegIn s;
+    s.start = 0;
+    s.m = (uint32_t)n;
+    s.k_hint = k1;
+    list_l1[0] = s;
+    st->nseg[1] = 1;  // level 1 reads list parity 1
+  }
+}
+
+// Per-segment parameters and prefix sums of one level (one CTA).
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads)
+k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, int par_in,
+             uint32_t kmax_level) {
+  __shared__ uint64_t sm[kPlanThreads / 32];
+  __shared__ uint64_t carry[6];
+  __shared__ uint32_t sG;
+  if (threadIdx.x == 0) {
+    uint32_t G = st->nseg[par_in];
+    st->nseg[par_in ^ 1] = 0;
+    if (G > P.seg_cap) {
+      atomicOr(&st->error, kErrSegCap);
+      G = 0;
+    }
+    if (G) st->levels_used = P.level;
+    sG = G;
+    for (int i = 0; i < 6; ++i) carry[i] = 0;
+  }
+  __syncthreads();
+  const uint32_t G = sG;
+  for (uint32_t base = 0; base < G; base += kPlanThreads) {
+    const uint32_t g = base + threadIdx.x;
+    uint64_t v[6] = {0, 0, 0, 0, 0, 0};
+    SegIn in{};
+    uint32_t k = 0, S = 0, nch = 0, nsch = 0;
+    if (g < G) {
+      in = list_in[g];
+      if (in.k_hint >= 1) {
+        k = min(in.k_hint, kmax_level);
+      } else {
+        const uint64_t want = ((uint64_t)in.m + kTargetBucket - 1) / kTargetBucket;
+        k = (uint32_t)umax64(2, umin64(want, kmax_level));
+      }
+      const uint64_t a = (in.k_hint >= 1 && P.level1_oversample)
+                             ? 16ull * ceil_log2_dev(k) : (uint64_t)kDeepOversample;
+      S = (uint32_t)umin64(in.m, a * k);
+      nch = (uint32_t)((in.m + (uint64_t)P.W - 1) / P.W);
+      nsch = (S + kSampleChunk - 1) / kSampleChunk;
+      v[0] = S;
+      v[1] = nch;
+      v[2] = (uint64_t)k * nch;
+      v[3] = nsch;
+      v[4] = k;
+      v[5] = in.m;
+    }
+    uint64_t ex[6], tot[6];
+    for (int i = 0; i < 6; ++i) ex[i] = block_excl_scan_u64<kPlanThreads>(v[i], &tot[i], sm);
+    if (g < G) {
+      LevelSeg s;
+      s.start = in.start;
+      s.seed = P.level == 1 ? P.seed
+                            : splitmix64_at(P.seed, ((uint64_t)P.level << 40) ^ in.start);
+      s.samp_off = carry[0] + ex[0];
+      s.chunk_off = carry[1] + ex[1];
+      s.hist_off = carry[2] + ex[2];
+      s.schunk_off = carry[3] + ex[3];
+      s.bkt_off = carry[4] + ex[4];
+      s.delta = in.start - (carry[5] + ex[5]);
+      s.m = in.m;
+      s.k = k;
+      s.S = S;
+      s.nchunks = nch;
+      s.nschunks = nsch;
+      s.pad = 0;
+      segs[g] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < 6; ++i) carry[i] += tot[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    uint32_t err = 0;
+    if (carry[0] > P.samp_cap) err |= kErrSampleCap;
+    if (carry[1] > P.chunk_cap) err |= kErrChunkCap;
+    if (carry[2] > P.hist_cap) err |= kErrHistCap;
+    if (carry[3] > P.schunk_cap) err |= kErrSchunkCap;
+    if (carry[4] > P.bucket_cap) err |= kErrBucketCap;
+    if (err) {
+      atomicOr(&st->error, err);
+      st->cur_nseg = 0;
+      st->total_samples = st->total_chunks = st->total_hist = 0;
+      st->total_schunks = st->total_buckets = 0;
+    } else {
+      st->cur_nseg = G;
+      st->total_samples = carry[0];
+      st->total_chunks = carry[1];
+      st->total_hist = carry[2];
+      st->total_schunks = carry[3];
+      st->total_buckets = carry[4];
+      if (P.level >= 1 && P.level <= 4) st->level_elems[P.level - 1] = carry[5];
+    }
+  }
+}
+
+// Step 1: stratified random samples, each carrying its position.  Sample j of
+// a segment of m elements with S samples comes from positions
+// [floor(j*m/S), floor((j+1)*m/S)) at offset splitmix64(seed, j) mod size.
+__global__ void __launch_bounds__(256)
+k_sample(const DevState* st, const LevelSeg* segs, Src src, uint64_t* samp_key,
+         uint32_t* samp_idx) {
+  const uint64_t total = st->total_samples;
+  const uint32_t G = st->cur_nseg;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+    const LevelSeg& sg = segs[g];
+    const uint64_t j = s - sg.samp_off;
+    const uint64_t lo = (j * sg.m) / sg.S, hi = ((j + 1) * sg.m) / sg.S;
+    const uint64_t pos = lo + splitmix64_at(sg.seed, j) % (hi - lo);
+    const uint64_t at = sg.start + pos;
+    samp_key[s] = load_key(src, at);
+    samp_idx[s] = src.idx ? src.idx[at] : (uint32_t)pos;
+  }
+}
+
+// Step 2a: sort chunks of up to kSampleChunk sample pairs in shared memory.
+// Single-chunk samples go straight to the sorted-sample array.
+__global__ void __launch_bounds__(512)
+k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_key,
+                     uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
+  __shared__ uint64_t sk[kSampleChunk];
+  __shared__ uint32_t si[kSampleChunk];
+  const uint64_t total = st->total_schunks;
+  const uint32_t G = st->cur_nseg;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.schunk_off; });
+    const LevelSeg sg = segs[g];
+    const uint64_t cl = c - sg.schunk_off;
+    const uint64_t base = sg.samp_off + cl * kSampleChunk;
+    const int len = (int)umin64(kSampleChunk, sg.S - cl * kSampleChunk);
+    const int P = (int)next_pow2_u32((uint32_t)len);
+    for (int t = threadIdx.x; t < P; t += 512) {
+      if (t < len) {
+        sk[t] = samp_key[base + t];
+        si[t] = samp_idx[base + t];
+      } else {
+        sk[t] = ~0ULL;
+        si[t] = ~0u;
+      }
+    }
+    block_bitonic_sort<512>(sk, si, P);
+    uint64_t* ok = sg.nschunks == 1 ? ssamp_key : samp_key;
+    uint32_t* oi = sg.nschunks == 1 ? ssamp_idx : samp_idx;
+    for (int t = threadIdx.x; t < len; t += 512) {
+      ok[base + t] = sk[t];
+      oi[base + t] = si[t];
+    }
+    __syncthreads();
+  }
+}
+
+// Step 2b: merge sorted chunks by ranking (the fast work-inefficient ranking
+// idea of Appendix "Fast Work-Inefficient Ranking": the rank of an element is
+// its rank in its own sorted sequence plus its ranks in the other sorted
+// sequences).
+__global__ void __launch_bounds__(256)
+k_sample_merge_rank(const DevState* st, const LevelSeg* segs, const uint64_t* samp_key,
+                    const uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
+  const uint64_t total = st->total_samples;
+  const uint32_t G = st->cur_nseg;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+    const LevelSeg& sg = segs[g];
+    if (sg.nschunks <= 1) continue;
+    const uint64_t j = s - sg.samp_off;
+    const uint32_t c = (uint32_t)(j / kSampleChunk);
+    const uint64_t myk = samp_key[s];
+    const uint32_t myi = samp_idx[s];
+    uint64_t rank = j - (uint64_t)c * kSampleChunk;
+    for (uint32_t c2 = 0; c2 < sg.nschunks; ++c2) {
+      if (c2 == c) continue;
+      const uint64_t b0 = sg.samp_off + (uint64_t)c2 * kSampleChunk;
+      const uint64_t len = umin64(kSampleChunk, sg.S - (uint64_t)c2 * kSampleChunk);
+      uint64_t lo = 0, hi = len;
+      while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (pair_less(samp_key[b0 + mid], samp_idx[b0 + mid], myk, myi)) lo = mid + 1;
+        else hi = mid;
+      }
+      rank += lo;
+    }
+    ssamp_key[sg.samp_off + rank] = myk;
+    ssamp_idx[sg.samp_off + rank] = myi;
+  }
+}
+
+// Shared-memory carve-up of the classify / scatter kernels.
+struct PartSmem {
+  Splitters sp;
+  uint32_t* hist;      // [K]   classify: counts;  scatter: running offsets
+  uint32_t* sbase;     // [K+1] scatter: sub-tile bucket starts
+  uint16_t* wcnt;      // [kPartWarps][K] scatter: per-warp counts / bases
+  uint64_t* stg_key;   // [kSubTile]
+  uint32_t* stg_idx;   // [kSubTile]
+  uint16_t* stg_b;     // [kSubTile]
+};
+
+// Per-warp counter rows are padded to an even length so a warp can clear its
+// row with 32-bit stores without touching the next warp's row.
+__host__ __device__ inline uint32_t cnt_stride(uint32_t kmax) { return (kmax + 1) & ~1u; }
+
+__host__ __device__ inline size_t part_smem_bytes(uint32_t kmax, bool scatter) {
+  const size_t Kp = next_pow2_u32(kmax);
+  size_t b = Kp * 8 + (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
+  if (scatter) {
+    b += (size_t)(kmax + 1) * 4 + 4;  // sbase, padded to 8 bytes
+    b += (size_t)kPartWarps * cnt_stride(kmax) * 2;
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)kSubTile * (8 + 4 + 2);
+  }
+  return b;
+}
+
+__device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatter) {
+  PartSmem s;
+  const size_t Kp = next_pow2_u32(kmax);
+  unsigned char* p = base;
+  s.sp.tree = (uint64_t*)p; p += Kp * 8;
+  s.sp.key = (uint64_t*)p; p += (size_t)kmax * 8;
+  s.sp.idx = (uint32_t*)p; p += (size_t)kmax * 4;
+  s.hist = (uint32_t*)p; p += (size_t)kmax * 4;
+  s.sbase = nullptr; s.wcnt = nullptr; s.stg_key = nullptr; s.stg_idx = nullptr;
+  s.stg_b = nullptr;
+  if (scatter) {
+    s.sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4 + 4;
+    s.wcnt = (uint16_t*)p; p += (size_t)kPartWarps * cnt_stride(kmax) * 2;
+    p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    s.stg_key = (uint64_t*)p; p += (size_t)kSubTile * 8;
+    s.stg_idx = (uint32_t*)p; p += (size_t)kSubTile * 4;
+    s.stg_b = (uint16_t*)p;
+  }
+  return s;
+}
+
+// Steps 4 + 5a: classify every element and count, per chunk of W elements,
+// how many fall into each bucket.  hist is laid out per segment bucket-major:
+// hist[hist_off + b * nchunks + chunk].
+__global__ void __launch_bounds__(kPartThreads)
+k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+                 const uint32_t* ssi, uint32_t* hist, uint32_t W, uint32_t kmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PartSmem sm = carve(smem_raw, kmax, false);
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    __syncthreads();
+    if (g != cur_g) {
+      load_splitters<kPartThreads>(sg, ssk, ssi, sm.sp);
+      cur_g = g;
+    }
+    for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads) sm.hist[b] = 0;
+    __syncthreads();
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * W;
+    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    for (uint64_t base = cs + (uint64_t)warp * kWarpSpan; base < ce;
+         base += (uint64_t)kPartWarps * kWarpSpan) {
+      uint64_t key[kItems];
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const uint64_t pos = base + r * 32 + lane;
+        key[r] = pos < ce ? load_key(src, pos) : 0;
+      }
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const uint64_t pos = base + r * 32 + lane;
+        const bool v = pos < ce;
+        // positions are read only when a key ties with a splitter key
+        const uint32_t b = classify(key[r], [&] {
+          return v ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0u;
+        }, sm.sp);
+        const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
+        if (__all_sync(0xffffffffu, v && b == b0)) {
+          if (lane == 0) atomicAdd(&sm.hist[b0], 32u);
+        } else if (v) {
+          atomicAdd(&sm.hist[b], 1u);
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads)
+      hist[sg.hist_off + (uint64_t)b * sg.nchunks + cl] = sm.hist[b];
+  }
+}
+
+// Step 5b: exclusive scan of the histogram counters (three launches).
+__global__ void __launch_bounds__(1024)
+k_scan_reduce(const DevState* st, const uint32_t* a, uint32_t* sums) {
+  __shared__ uint64_t sm[32];
+  const uint64_t total = st->total_hist;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  if (base >= total) return;
+  uint64_t v = 0;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = base + threadIdx.x * 4 + r;
+    if (i < total) v += a[i];
+  }
+  uint64_t tot;
+  block_excl_scan_u64<1024>(v, &tot, sm);
+  if (threadIdx.x == 0) sums[blockIdx.x] = (uint32_t)tot;
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_sums(const DevState* st, uint32_t* sums) {
+  __shared__ uint64_t sm[32];
+  const uint64_t total = st->total_hist;
+  const uint64_t ntiles = (total + kScanTile - 1) / kScanTile;
+  uint64_t carry = 0;
+  for (uint64_t b = 0; b < ntiles; b += 1024) {
+    const uint64_t i = b + threadIdx.x;
+    const uint64_t v = i < ntiles ? sums[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_excl_scan_u64<1024>(v, &tot, sm);
+    if (i < ntiles) sums[i] = (uint32_t)(carry + ex);
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan_down(const DevState* st, uint32_t* a, const uint32_t* sums) {
+  __shared__ uint64_t sm[32];
+  const uint64_t total = st->total_hist;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  if (base >= total) return;
+  uint32_t x[4];
+  uint64_t v = 0;
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = base + threadIdx.x * 4 + r;
+    x[r] = i < total ? a[i] : 0;
+    v += x[r];
+  }
+  uint64_t tot;
+  uint64_t run = block_excl_scan_u64<1024>(v, &tot, sm) + sums[blockIdx.x];
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t i = base + threadIdx.x * 4 + r;
+    if (i < total) a[i] = (uint32_t)run;
+    run += x[r];
+  }
+}
+
+// Step 5c: stable scatter.  Every chunk is processed in sub-tiles of kSubTile
+// elements; warp w owns 512 consecutive elements of the sub-tile.  Each
+// element's rank among the earlier elements of its bucket in the sub-tile is
+// computed with warp-synchronous match/ballot counting (warp order, then
+// lane order = input order), the sub-tile is counting-sorted by bucket in
+// shared memory, and runs of each bucket are written out contiguously
+// (write-combining through shared memory).  Buckets therefore keep input order.
+__global__ void __launch_bounds__(kPartThreads)
+k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+          const uint32_t* ssi, const uint32_t* hist_scan, Dst dst, uint32_t W, uint32_t kmax,
+          int unmap_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PartSmem sm = carve(smem_raw, kmax, true);
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t ltmask = lanemask_lt();
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    __syncthreads();
+    if (g != cur_g) {
+      load_splitters<kPartThreads>(sg, ssk, ssi, sm.sp);
+      cur_g = g;
+    }
+    const uint32_t k = sg.k;
+    const uint64_t cl = c - sg.chunk_off;
+    for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
+      sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nchunks + cl] + sg.delta);
+    const uint64_t cs = sg.start + cl * W;
+    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    const uint32_t kst = cnt_stride(kmax);
+    uint16_t* my_cnt = sm.wcnt + (size_t)warp * kst;
+    for (uint64_t sub = cs; sub < ce; sub += kSubTile) {
+      const uint32_t len = (uint32_t)umin64(kSubTile, ce - sub);
+      const uint64_t wbase = sub + (uint64_t)warp * kWarpSpan;
+      uint64_t key[kItems];
+      uint32_t idx[kItems];
+      uint32_t bk[kItems];
+      uint32_t lrank[kItems];
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const uint64_t pos = wbase + r * 32 + lane;
+        const bool v = pos < ce;
+        key[r] = v ? load_key(src, pos) : 0;
+        idx[r] = v ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0;
+      }
+      for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const uint64_t pos = wbase + r * 32 + lane;
+        const bool v = pos < ce;
+        const uint32_t b = v ? classify(key[r], [&] { return idx[r]; }, sm.sp) : 0xffffffffu;
+        bk[r] = b;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const uint32_t c0 = v ? my_cnt[b] : 0;
+        __syncwarp();
+        if (v && lane == __ffs(peers) - 1) my_cnt[b] = (uint16_t)(c0 + __popc(peers));
+        __syncwarp();
+        lrank[r] = c0 + __popc(peers & ltmask);
+      }
+      __syncthreads();
+      // per bucket: exclusive prefix over warps (in place) and the sub-tile total
+      for (uint32_t b = threadIdx.x; b < k; b += kPartThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kPartWarps; ++w) {
+          const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
+          sm.wcnt[(size_t)w * kst + b] = (uint16_t)s;
+          s += cnt;
+        }
+        sm.sbase[b] = s;
+      }
+      __syncthreads();
+      // exclusive scan of the k sub-tile totals (one thread per run of buckets)
+      {
+        const uint32_t per = (k + kPartThreads - 1) / kPartThreads;
+        const uint32_t b0 = threadIdx.x * per;
+        uint32_t loc = 0;
+        for (uint32_t b = b0; b < min(k, b0 + per); ++b) loc += sm.sbase[b];
+        uint64_t tot;
+        __shared__ uint64_t scan_sm[kPartWarps];
+        uint32_t run = (uint32_t)block_excl_scan_u64<kPartThreads>(loc, &tot, scan_sm);
+        for (uint32_t b = b0; b < min(k, b0 + per); ++b) {
+          const uint32_t t = sm.sbase[b];
+          sm.sbase[b] = run;
+          run += t;
+        }
+        if (threadIdx.x == 0) sm.sbase[k] = len;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) {
+        const uint32_t b = bk[r];
+        if (b != 0xffffffffu) {
+          const uint32_t q = sm.sbase[b] + my_cnt[b] + lrank[r];
+          sm.stg_key[q] = key[r];
+          sm.stg_idx[q] = idx[r];
+          sm.stg_b[q] = (uint16_t)b;
+        }
+      }
+      __syncthreads();
+      for (uint32_t q = threadIdx.x; q < len; q += kPartThreads) {
+        const uint32_t b = sm.stg_b[q];
+        const uint64_t d = (uint64_t)sm.hist[b] + (q - sm.sbase[b]);
+        const uint64_t kv = sm.stg_key[q];
+        dst.key[d] = unmap_out ? ordered_to_f64(kv) : kv;
+        dst.idx[d] = sm.stg_idx[q];
+      }
+      __syncthreads();
+      for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
+        sm.hist[b] += sm.sbase[b + 1] - sm.sbase[b];
+      __syncthreads();
+    }
+  }
+}
+
+// Collect the buckets of the level: bucket sizes follow from the scanned
+// histogram.  Buckets that fit one SM, equality buckets (both bounding
+// splitters share one key, so every element has that key and the stable
+// scatter already left them in position order) and empty ones are final;
+// the rest become segments of the next level.
+__global__ void __launch_bounds__(256)
+k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_t* hist_scan,
+          SegIn* list_out, int par_out, FinalItem* items, LevelParams P, uint16_t where,
+          int last_level, int emit_final, uint64_t* offsets_out) {
+  const uint64_t total = st->total_buckets;
+  const uint32_t G = st->cur_nseg;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_seg(segs, G, f, [](const LevelSeg& x) { return x.bkt_off; });
+    const LevelSeg& sg = segs[g];
+    const uint32_t b = (uint32_t)(f - sg.bkt_off);
+    const uint64_t start = hist_scan[sg.hist_off + (uint64_t)b * sg.nchunks] + sg.delta;
+    const uint64_t end = (b + 1 < sg.k)
+                             ? hist_scan[sg.hist_off + (uint64_t)(b + 1) * sg.nchunks] + sg.delta
+                             : sg.start + sg.m;
+    const uint32_t size = (uint32_t)(end - start);
+    if (offsets_out) {
+      offsets_out[b] = start - sg.start;
+      if (b == 0) offsets_out[sg.k] = sg.m;
+    }
+    if (P.level == 1) atomicMax(&st->max_bucket_l1, size);
+    if (!emit_final || size == 0) continue;
+    bool eq = false;
+    if (b >= 1 && b + 1 < sg.k) {
+      const uint64_t klo = ssk[sg.samp_off + ((uint64_t)b * sg.S) / sg.k];
+      const uint64_t khi = ssk[sg.samp_off + ((uint64_t)(b + 1) * sg.S) / sg.k];
+      eq = klo == khi;
+    }
+    if (eq || size <= kBucketCap || last_level) {
+      FinalItem it;
+      it.start = start;
+      it.idx_base = 0;
+      it.size = size;
+      it.where = where;
+      it.kind = (eq || size == 1) ? kKindCopy : (size <= kBucketCap ? kKindSort : kKindBig);
+      if (it.kind == kKindBig) atomicAdd((unsigned long long*)&st->big_items, 1ull);
+      const uint32_t slot = atomicAdd(&st->nfinal, 1u);
+      if (slot < P.final_cap) items[slot] = it;
+      else atomicOr(&st->error, kErrFinalCap);
+    } else {
+      SegIn s;
+      s.start = start;
+      s.m = size;
+      s.k_hint = 0;
+      const uint32_t slot = atomicAdd(&st->nseg[par_out], 1u);
+      if (slot < P.seg_cap) list_out[slot] = s;
+      else atomicOr(&st->error, kErrSegCap);
+    }
+  }
+}
+
+inline int grid_for(uint64_t work, int per_block, int max_blocks) {
+  uint64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  return (int)umin64(b, (uint64_t)max_blocks);
+}
+
+}  // namespace
+
+void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
+                       uint64_t n, uint32_t k1, int direct) {
+  Scope sc(e, "init");
+  k_init_plain<<<1, 32, 0, e.stream>>>(st, list0, items, n, k1, direct);
+}
+
+size_t part_smem_bytes_host(uint32_t kmax, bool scatter) { return part_smem_bytes(kmax, scatter); }
+
+void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const SegIn* list_in,
+                  SegIn* list_out, LevelSeg* segs, Src src, Dst dst, uint16_t dst_where,
+                  uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,
+                  uint32_t* ssamp_idx, uint32_t* hist, uint32_t* block_sums, FinalItem* items,
+                  int kmax_level, int last_level, int emit_final, uint64_t* offsets_out,
+                  uint64_t /*n_total*/, int unmap_out) {
+  const int par_in = P.level & 1;
+  const int sms = e.num_sms;
+  static const char* kNames[kMaxLevels + 1][10] = {
+      {"L?.plan", "L?.sample", "L?.sample_sort", "L?.sample_merge", "L?.classify",
+       "L?.scan_reduce", "L?.scan_sums", "L?.scan_down", "L?.scatter", "L?.collect"},
+      {"L1.plan", "L1.sample", "L1.sample_sort", "L1.sample_merge", "L1.classify",
+       "L1.scan_reduce", "L1.scan_sums", "L1.scan_down", "L1.scatter", "L1.collect"},
+      {"L2.plan", "L2.sample", "L2.sample_sort", "L2.sample_merge", "L2.classify",
+       "L2.scan_reduce", "L2.scan_sums", "L2.scan_down", "L2.scatter", "L2.collect"},
+      {"L3.plan", "L3.sample", "L3.sample_sort", "L3.sample_merge", "L3.classify",
+       "L3.scan_reduce", "L3.scan_sums", "L3.scan_down", "L3.scatter", "L3.collect"}};
+  const char* const* nm = kNames[(P.level >= 1 && P.level <= kMaxLevels) ? P.level : 0];
+  {
+    Scope sc(e, nm[0]);
+    k_level_plan<<<1, kPlanThreads, 0, e.stream>>>(st, list_in, segs, P, par_in,
+                                                  (uint32_t)kmax_level);
+  }
+  {
+    Scope sc(e, nm[1]);
+    k_sample<<<grid_for(P.samp_cap, 256, sms * 8), 256, 0, e.stream>>>(st, segs, src, samp_key,
+                                                                       samp_idx);
+  }
+  {
+    Scope sc(e, nm[2]);
+    k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms * 2), 512, 0, e.stream>>>(
+        st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
+  }
+  {
+    Scope sc(e, nm[3]);
+    k_sample_merge_rank<<<grid_for(P.samp_cap, 256, sms * 8), 256, 0, e.stream>>>(
+        st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
+  }
+  const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false);
+  const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true);
+  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)part_smem_bytes(kMaxK, false));
+  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)part_smem_bytes(kMaxK, true));
+  const int part_grid = grid_for(P.chunk_cap, 1, sms * 2);
+  {
+    Scope sc(e, nm[4]);
+    k_classify_count<<<part_grid, kPartThreads, smem_c, e.stream>>>(
+        st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level);
+  }
+  const int scan_grid = (int)((P.hist_cap + kScanTile - 1) / kScanTile);
+  {
+    Scope sc(e, nm[5]);
+    k_scan_reduce<<<scan_grid > 0 ? scan_grid : 1, 1024, 0, e.stream>>>(st, hist, block_sums);
+  }
+  {
+    Scope sc(e, nm[6]);
+    k_scan_sums<<<1, 1024, 0, e.stream>>>(st, block_sums);
+  }
+  {
+    Scope sc(e, nm[7]);
+    k_scan_down<<<scan_grid > 0 ? scan_grid : 1, 1024, 0, e.stream>>>(st, hist, block_sums);
+  }
+  {
+    Scope sc(e, nm[8]);
+    k_scatter<<<part_grid, kPartThreads, smem_s, e.stream>>>(
+        st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out);
+  }
+  {
+    Scope sc(e, nm[9]);
+    k_collect<<<grid_for(P.bucket_cap, 256, sms * 8), 256, 0, e.stream>>>(
+        st, segs, ssamp_key, hist, list_out, par_in ^ 1, items, P, dst_where, last_level,
+        emit_final, offsets_out);
+  }
+}
+
+}  // namespace rsort

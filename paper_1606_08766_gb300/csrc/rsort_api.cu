@@ -1,0 +1,532 @@
+// rsort_api.cu -- the C ABI of librsort (see include/rsort.h): context and
+// scratch management, the host-side plan of a sort, and the launch sequence.
+//
+// Host code here only validates arguments, sizes scratch and enqueues kernels;
+// every step of the method runs in the kernels of partition_kernels.cu and
+// local_sort_kernels.cu.  Nothing here synchronises unless a caller asks for
+// a read-back (stats, rsort_check, phase times).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "rsort_internal.cuh"
+
+namespace rsort {
+size_t part_smem_bytes_host(uint32_t kmax, bool scatter);
+
+// ---------------------------------------------------------------------------
+// Kernel timer: a pair of CUDA events around every launch, resolved lazily.
+// ---------------------------------------------------------------------------
+struct TimerImpl {
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> open;
+  std::vector<cudaEvent_t> pool;
+  std::unordered_map<std::string, std::pair<double, uint64_t>> acc;
+  std::vector<std::string> order;
+  const char* pending = nullptr;
+  cudaEvent_t pending_ev = nullptr;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void resolve() {
+    for (auto& r : open) {
+      cudaEventSynchronize(r.b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      auto it = acc.find(r.name);
+      if (it == acc.end()) {
+        order.push_back(r.name);
+        acc[r.name] = {ms, 1};
+      } else {
+        it->second.first += ms;
+        it->second.second += 1;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    open.clear();
+  }
+  ~TimerImpl() {
+    for (auto& r : open) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+void KernelTimer::begin(const char* name, cudaStream_t s) {
+  TimerImpl* t = (TimerImpl*)impl;
+  t->pending = name;
+  t->pending_ev = t->get();
+  cudaEventRecord(t->pending_ev, s);
+}
+void KernelTimer::end(cudaStream_t s) {
+  TimerImpl* t = (TimerImpl*)impl;
+  cudaEvent_t b = t->get();
+  cudaEventRecord(b, s);
+  t->open.push_back({t->pending, t->pending_ev, b});
+}
+
+}  // namespace rsort
+
+using namespace rsort;
+
+struct rsort_ctx {
+  int device = 0;
+  int num_sms = 0;
+  uint64_t budget = 0;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  rsort_status latched = RSORT_OK;
+  DevState* h_state = nullptr;  // pinned read-back buffer
+  uint64_t launches = 0;
+  bool profiling = false;
+  KernelTimer timer;
+  TimerImpl timer_impl;
+  std::mutex mu;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Scratch plan of one sort / partition call.
+struct Plan {
+  uint64_t n = 0;
+  uint32_t k1 = 0;          // level-1 buckets (0: automatic)
+  int levels = 0;           // partition levels to launch
+  int direct = 0;           // n small enough for one in-SM sort
+  uint32_t W1 = 0, Wd = 0;  // chunk sizes (level 1, deeper levels)
+  uint64_t seg_cap = 0, samp_cap = 0, hist_cap = 0, chunk_cap = 0, schunk_cap = 0;
+  uint64_t bucket_cap = 0, final_cap = 0;
+  uint64_t samp_cap1 = 0, hist_cap1 = 0, chunk_cap1 = 0, schunk_cap1 = 0, bucket_cap1 = 0;
+  bool need_tmp = false;
+  // arena offsets
+  size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
+  size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
+  size_t off_list0 = 0, off_list1 = 0, off_items = 0, off_state = 0, total = 0;
+};
+
+uint32_t ceil_log2_host(uint32_t k) {
+  uint32_t l = 0;
+  while ((1ull << l) < k) ++l;
+  return l;
+}
+
+void layout(Plan& p) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + (bytes ? bytes : 16), 256);
+    return at;
+  };
+  p.off_state = take(sizeof(DevState));
+  p.off_items = take(p.final_cap * sizeof(FinalItem));
+  if (p.need_tmp) {
+    p.off_tmp_key = take(p.n * 8);
+    p.off_tmp_idx = take(p.n * 4);
+  }
+  p.off_samp_key = take(p.samp_cap * 8);
+  p.off_samp_idx = take(p.samp_cap * 4);
+  p.off_ssamp_key = take(p.samp_cap * 8);
+  p.off_ssamp_idx = take(p.samp_cap * 4);
+  p.off_hist = take(p.hist_cap * 4);
+  p.off_sums = take((p.hist_cap / kScanTile + 2) * 4);
+  p.off_segs = take(p.seg_cap * sizeof(LevelSeg));
+  p.off_list0 = take(p.seg_cap * sizeof(SegIn));
+  p.off_list1 = take(p.seg_cap * sizeof(SegIn));
+  p.total = o;
+}
+
+// Capacities of the sample-sort levels for n elements, level-1 fan-out k1
+// (0: automatic) and g1 level-1 segments.
+void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int levels) {
+  p.n = n;
+  p.k1 = k1;
+  p.levels = levels;
+  const uint64_t per = (n + 2ull * num_sms - 1) / (2ull * num_sms);
+  p.W1 = (uint32_t)std::max<uint64_t>(kSubTile, align_up(per, kSubTile));
+  if (g1 > 1) p.W1 = 65536;
+  p.Wd = 65536;
+  const uint64_t segs_deep = n / (kBucketCap + 1) + 1;
+  p.seg_cap = std::max<uint64_t>(g1, segs_deep);
+  const uint32_t kmax1 = k1 >= 2 ? k1 : kMaxKDeep;
+  // level 1
+  p.bucket_cap1 = k1 >= 2 ? (uint64_t)k1 * g1 : n / kTargetBucket + g1 + 1;
+  p.bucket_cap1 = std::min<uint64_t>(p.bucket_cap1, (uint64_t)kmax1 * g1);
+  const uint64_t a1 = k1 >= 2 ? 16ull * ceil_log2_host(k1) : (uint64_t)kDeepOversample;
+  p.samp_cap1 = std::min<uint64_t>(n, a1 * p.bucket_cap1);
+  p.chunk_cap1 = n / p.W1 + g1 + 1;
+  p.hist_cap1 = (uint64_t)kmax1 * (n / p.W1) + p.bucket_cap1;
+  p.schunk_cap1 = p.samp_cap1 / kSampleChunk + g1 + 1;
+  // deeper levels
+  const uint64_t bucket_capd = n / kTargetBucket + segs_deep + 1;
+  const uint64_t samp_capd = std::min<uint64_t>(n, (uint64_t)kDeepOversample * bucket_capd);
+  const uint64_t chunk_capd = n / p.Wd + segs_deep + 1;
+  const uint64_t hist_capd = (uint64_t)kMaxKDeep * (n / p.Wd) + bucket_capd;
+  const uint64_t schunk_capd = samp_capd / kSampleChunk + segs_deep + 1;
+  const bool deep = levels > 1;
+  p.bucket_cap = std::max<uint64_t>(p.bucket_cap1, deep ? bucket_capd : 0);
+  p.samp_cap = std::max<uint64_t>(p.samp_cap1, deep ? samp_capd : 0);
+  p.chunk_cap = std::max<uint64_t>(p.chunk_cap1, deep ? chunk_capd : 0);
+  p.hist_cap = std::max<uint64_t>(p.hist_cap1, deep ? hist_capd : 0);
+  p.schunk_cap = std::max<uint64_t>(p.schunk_cap1, deep ? schunk_capd : 0);
+  p.final_cap = p.bucket_cap1 + (uint64_t)(levels - 1) * bucket_capd + 4;
+}
+
+LevelParams level_params(const Plan& p, int level, uint64_t seed) {
+  LevelParams P;
+  P.level = level;
+  P.W = level == 1 ? p.W1 : p.Wd;
+  P.seed = seed;
+  P.seg_cap = p.seg_cap;
+  P.final_cap = p.final_cap;
+  if (level == 1) {
+    P.samp_cap = p.samp_cap1;
+    P.hist_cap = p.hist_cap1;
+    P.chunk_cap = p.chunk_cap1;
+    P.schunk_cap = p.schunk_cap1;
+    P.bucket_cap = p.bucket_cap1;
+  } else {
+    P.samp_cap = p.samp_cap;
+    P.hist_cap = p.hist_cap;
+    P.chunk_cap = p.chunk_cap;
+    P.schunk_cap = p.schunk_cap;
+    P.bucket_cap = p.bucket_cap;
+  }
+  P.level1_oversample = 1;
+  return P;
+}
+
+rsort_status latch(rsort_ctx* c, rsort_status s) {
+  if (s != RSORT_OK && c->latched == RSORT_OK) c->latched = s;
+  return s;
+}
+
+rsort_status cuda_status(rsort_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return RSORT_OK;
+  if (e == cudaErrorMemoryAllocation) return latch(c, RSORT_ENOMEM);
+  return latch(c, RSORT_ECUDA);
+}
+
+rsort_status ensure_arena(rsort_ctx* c, size_t bytes, cudaStream_t s) {
+  if (bytes <= c->arena_bytes) return RSORT_OK;
+  if (c->budget && bytes > c->budget) return RSORT_ENOMEM;
+  if (c->arena) {
+    cudaFreeAsync(c->arena, s);
+    c->arena = nullptr;
+    c->arena_bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return RSORT_ENOMEM;
+  }
+  c->arena = p;
+  c->arena_bytes = bytes;
+  return RSORT_OK;
+}
+
+template <typename T>
+T* at(rsort_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(c->arena) + off);
+}
+
+LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
+  LaunchEnv e;
+  e.stream = s;
+  e.num_sms = c->num_sms;
+  e.timer = c->profiling ? &c->timer : nullptr;
+  e.launches = &c->launches;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rsort_strerror(rsort_status s) {
+  switch (s) {
+    case RSORT_OK: return "ok";
+    case RSORT_PENDING: return "pending";
+    case RSORT_EINVAL: return "invalid argument";
+    case RSORT_ENOMEM: return "out of memory (scratch exceeds budget or device memory)";
+    case RSORT_ECUDA: return "CUDA error";
+    case RSORT_ETIMEOUT: return "timed out";
+    case RSORT_ECANCELLED: return "cancelled";
+    case RSORT_EUNSUPPORTED: return "unsupported";
+    case RSORT_EDEVICE: return "device-side error (capacity check failed)";
+    default: return "unknown status";
+  }
+}
+
+rsort_status rsort_create(rsort_ctx** out, int device, uint64_t hbm_budget_bytes,
+                          const char* tune_table_path) {
+  if (!out) return RSORT_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return RSORT_EINVAL;
+  }
+  if (tune_table_path) {
+    FILE* f = fopen(tune_table_path, "r");
+    if (!f) return RSORT_EINVAL;
+    fclose(f);
+  }
+  rsort_ctx* c = new (std::nothrow) rsort_ctx();
+  if (!c) return RSORT_ENOMEM;
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  DeviceGuard g(device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(&c->h_state, sizeof(DevState)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return RSORT_ECUDA;
+  }
+  c->timer.impl = &c->timer_impl;
+  *out = c;
+  return RSORT_OK;
+}
+
+rsort_status rsort_destroy(rsort_ctx* c) {
+  if (!c) return RSORT_OK;
+  {
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    if (c->arena) cudaFree(c->arena);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    cudaGetLastError();
+  }
+  delete c;
+  return RSORT_OK;
+}
+
+rsort_status rsort_check(rsort_ctx* c) {
+  if (!c) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) latch(c, RSORT_ECUDA);
+  cuda_status(c);
+  if (c->arena) {
+    DevState st;
+    if (cudaMemcpy(&st, c->arena, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess)
+      latch(c, RSORT_ECUDA);
+    else if (st.error)
+      latch(c, RSORT_EDEVICE);
+  }
+  rsort_status s = c->latched;
+  c->latched = RSORT_OK;
+  return s;
+}
+
+rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                             uint64_t n, uint32_t k, uint64_t seed, void* d_keys_out,
+                             uint32_t* d_pos_out, uint64_t* d_offsets_out, void* stream) {
+  if (!c || (type != RSORT_KEY_U64 && type != RSORT_KEY_F64)) return RSORT_EINVAL;
+  if (k < 1 || k > (uint32_t)kMaxK || n > 0xFFFFFFFFull) return RSORT_EINVAL;
+  if (!d_offsets_out || (n > 0 && (!d_keys_in || !d_keys_out || !d_pos_out)))
+    return RSORT_EINVAL;
+  if (n > 0 && d_keys_in == d_keys_out) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->latched != RSORT_OK) {
+    rsort_status s = c->latched;
+    c->latched = RSORT_OK;
+    return s;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  LaunchEnv e = env_of(c, s);
+  if (n == 0) {
+    // every bucket is empty
+    cudaMemsetAsync(d_offsets_out, 0, (size_t)(k + 1) * 8, s);
+    return cuda_status(c);
+  }
+  Plan p;
+  const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
+  plan_levels(p, n, kk, 1, c->num_sms, 1);
+  p.final_cap = 4;
+  p.need_tmp = false;
+  layout(p);
+  rsort_status rs = ensure_arena(c, p.total, s);
+  if (rs != RSORT_OK) return latch(c, rs);
+  DevState* st = at<DevState>(c, p.off_state);
+  SegIn* list1 = at<SegIn>(c, p.off_list1);
+  launch_init_plain(e, st, list1, at<FinalItem>(c, p.off_items), n, k, 0);
+  LevelParams P = level_params(p, 1, seed);
+  Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
+  Dst dst{(uint64_t*)d_keys_out, d_pos_out};
+  launch_level(e, P, st, list1, at<SegIn>(c, p.off_list0), at<LevelSeg>(c, p.off_segs), src, dst,
+               kWhereOut, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
+               at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
+               at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums),
+               at<FinalItem>(c, p.off_items), (int)kk, 1, 0, d_offsets_out, n,
+               type == RSORT_KEY_F64);
+  return cuda_status(c);
+}
+
+rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                        void* d_keys_out, uint32_t* d_perm_out, uint64_t n, uint32_t p_virtual,
+                        uint64_t seed, void* stream, rsort_stats* opt_stats) {
+  if (!c || (type != RSORT_KEY_U64 && type != RSORT_KEY_F64)) return RSORT_EINVAL;
+  if (n > 0xFFFFFFFFull || p_virtual < 1 || p_virtual > (uint32_t)kMaxK) return RSORT_EINVAL;
+  if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->latched != RSORT_OK) {
+    rsort_status s = c->latched;
+    c->latched = RSORT_OK;
+    return s;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (opt_stats) memset(opt_stats, 0, sizeof(*opt_stats));
+  if (n == 0) return RSORT_OK;
+  LaunchEnv e = env_of(c, s);
+  Plan p;
+  const int direct = n <= (uint64_t)kBucketCap;
+  const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
+  if (direct) {
+    p.n = n;
+    p.final_cap = 4;
+    p.seg_cap = 1;
+    p.need_tmp = false;
+  } else {
+    plan_levels(p, n, k1, 1, c->num_sms, kMaxLevels);
+    p.need_tmp = true;
+  }
+  layout(p);
+  rsort_status rs = ensure_arena(c, p.total, s);
+  if (rs != RSORT_OK) return latch(c, rs);
+  DevState* st = at<DevState>(c, p.off_state);
+  FinalItem* items = at<FinalItem>(c, p.off_items);
+  SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
+  launch_init_plain(e, st, lists[1], items, n, k1, direct);
+  Dst out{(uint64_t*)d_keys_out, d_perm_out};
+  Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
+  if (!direct) {
+    for (int L = 1; L <= p.levels; ++L) {
+      LevelParams P = level_params(p, L, seed);
+      Src src;
+      if (L == 1) {
+        src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
+      } else {
+        const Dst& prev = ((L - 1) & 1) ? tmp : out;
+        src = Src{prev.key, prev.idx, 0};
+      }
+      const Dst& dst = (L & 1) ? tmp : out;
+      const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
+      const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
+      launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(c, p.off_segs), src,
+                   dst, where, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
+                   at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
+                   at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums), items, kmax,
+                   L == p.levels, 1, nullptr, n, 0);
+    }
+  }
+  launch_local_sort(e, st, items, p.final_cap, (const uint64_t*)d_keys_in, out, tmp,
+                    type == RSORT_KEY_F64);
+  rs = cuda_status(c);
+  if (rs != RSORT_OK) return rs;
+  if (opt_stats) {
+    if (cudaMemcpyAsync(c->h_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return latch(c, RSORT_ECUDA);
+    const DevState& h = *c->h_state;
+    opt_stats->n = n;
+    opt_stats->p = direct ? 1 : (k1 >= 2 ? k1 : 0);
+    opt_stats->levels = h.levels_used;
+    opt_stats->path = direct ? 0 : 1;
+    opt_stats->max_bucket = direct ? (uint32_t)n : h.max_bucket_l1;
+    const double mean = opt_stats->p ? (double)n / opt_stats->p : (double)n;
+    opt_stats->max_over_mean = mean > 0 ? opt_stats->max_bucket / mean : 0.0;
+    opt_stats->final_buckets = h.nfinal;
+    // level 1 reads 8 B/key twice and writes 12; deeper levels read 8 + 12 and
+    // write 12; the in-SM sort reads and writes 12 B/key.
+    uint64_t bytes = 24ull * n;
+    for (int i = 0; i < 4; ++i) {
+      opt_stats->level_elems[i] = h.level_elems[i];
+      bytes += (i == 0 ? 28ull : 32ull) * h.level_elems[i];
+    }
+    opt_stats->bytes_moved = bytes;
+    if (h.error) return latch(c, RSORT_EDEVICE);
+  }
+  return RSORT_OK;
+}
+
+rsort_status rsort_set_profiling(rsort_ctx* c, int enable) {
+  if (!c) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->profiling = enable != 0;
+  return RSORT_OK;
+}
+
+rsort_status rsort_phase_times(rsort_ctx* c, const char** names, double* ms, uint64_t* launches,
+                               int max, int* count) {
+  if (!c || !count) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  c->timer_impl.resolve();
+  int i = 0;
+  for (const std::string& nm : c->timer_impl.order) {
+    if (i < max) {
+      auto& a = c->timer_impl.acc[nm];
+      // names point at the static literals used at launch time
+      static std::mutex name_mu;
+      static std::unordered_map<std::string, std::string> interned;
+      std::lock_guard<std::mutex> lk2(name_mu);
+      auto it = interned.emplace(nm, nm).first;
+      if (names) names[i] = it->second.c_str();
+      if (ms) ms[i] = a.first;
+      if (launches) launches[i] = a.second;
+    }
+    ++i;
+  }
+  *count = i;
+  c->timer_impl.acc.clear();
+  c->timer_impl.order.clear();
+  return cuda_status(c);
+}
+
+rsort_status rsort_launch_count(rsort_ctx* c, uint64_t* out) {
+  if (!c || !out) return RSORT_EINVAL;
+  *out = c->launches;
+  return RSORT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// rsort_internal.cuh -- device-side data structures, constants and helpers of
+// librsort (robust multi-level sample sort on one GB300).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rsort.h"
+
+namespace rsort {
+
+// ---------------------------------------------------------------------------
+// Tunables (defaults; a tune table may override the host-side ones)
+// ---------------------------------------------------------------------------
+constexpr int kPartThreads = 256;                 // classify / scatter CTA
+constexpr int kPartWarps = kPartThreads / 32;
+constexpr int kItems = 16;                        // keys per lane per sub-tile
+constexpr int kWarpSpan = 32 * kItems;            // 512 consecutive keys per warp
+constexpr int kSubTile = kPartThreads * kItems;   // 4096 keys staged per sub-tile
+constexpr int kMaxK = 2048;                       // buckets per partition step
+constexpr int kMaxKDeep = 512;                    // buckets at levels >= 2
+constexpr int kBucketCap = 4096;                  // T_s: largest bucket one CTA sorts
+constexpr int kTargetBucket = 1024;               // aim for this final bucket size
+constexpr int kSampleChunk = 4096;                // sample sort: pairs per CTA chunk
+constexpr int kDeepOversample = 16;               // samples per bucket at levels >= 2
+constexpr int kMaxLevels = 3;                     // partition levels before fallback
+constexpr int kLocalThreads = 512;                // in-SM bucket sort CTA
+constexpr int kRankMax = 64;                      // rank-by-counting up to this size
+constexpr int kScanTile = 4096;                   // device scan tile (1024 x 4)
+
+// Where the elements of a final bucket live.
+enum : uint16_t { kWhereOut = 0, kWhereTmp = 1, kWhereInput = 2 };
+// How a final bucket is finished.
+enum : uint16_t { kKindSort = 0, kKindCopy = 1, kKindBig = 2 };
+
+// A segment waiting to be partitioned (input of a level).
+struct SegIn {
+  uint64_t start;   // absolute position (identical in every buffer)
+  uint32_t m;       // elements
+  uint32_t k_hint;  // buckets requested (>= 1), or 0 to choose from m
+};
+
+// A segment being partitioned at the current level (written by the plan).
+struct LevelSeg {
+  uint64_t start;
+  uint64_t seed;
+  uint64_t samp_off;    // first sample slot
+  uint64_t chunk_off;   // first global chunk id
+  uint64_t hist_off;    // first histogram counter
+  uint64_t schunk_off;  // first sample-sort chunk id
+  uint64_t bkt_off;     // first global bucket id
+  uint64_t delta;       // start - (sum of sizes of earlier segments), mod 2^64
+  uint32_t m;
+  uint32_t k;
+  uint32_t S;
+  uint32_t nchunks;
+  uint32_t nschunks;
+  uint32_t pad;
+};
+
+// A bucket handed to the in-SM sort.
+struct FinalItem {
+  uint64_t start;     // absolute position of its first element
+  uint64_t idx_base;  // position - idx_base = original position (input only)
+  uint32_t size;
+  uint16_t where;
+  uint16_t kind;
+};
+
+// Device-resident control block of one call.
+struct DevState {
+  uint32_t nseg[2];         // segment lists (ping-pong by level parity)
+  uint32_t nfinal;          // final items
+  uint32_t final_cursor;    // work counter of the in-SM sort
+  uint32_t error;           // capacity / wait errors (bit flags)
+  uint32_t max_bucket_l1;   // largest level-1 bucket
+  uint32_t levels_used;
+  uint32_t cur_nseg;        // segments of the level being processed
+  uint64_t total_samples;
+  uint64_t total_chunks;
+  uint64_t total_hist;
+  uint64_t total_schunks;
+  uint64_t total_buckets;
+  uint64_t big_items;       // buckets that needed the oversize fallback
+  uint64_t level_elems[4];  // elements partitioned at levels 1..4
+};
+
+enum : uint32_t {
+  kErrSampleCap = 1u << 0,
+  kErrHistCap = 1u << 1,
+  kErrChunkCap = 1u << 2,
+  kErrSegCap = 1u << 3,
+  kErrFinalCap = 1u << 4,
+  kErrSchunkCap = 1u << 5,
+  kErrBucketCap = 1u << 6,
+};
+
+// Parameters of one level, fixed on the host.
+struct LevelParams {
+  int level;            // 1-based
+  uint32_t W;           // keys per classify/scatter chunk
+  uint64_t seed;
+  uint64_t samp_cap, hist_cap, chunk_cap, seg_cap, final_cap, schunk_cap, bucket_cap;
+  int level1_oversample;  // 1: a = 16 ceil(log2 k) for hinted k (the paper's rule)
+};
+
+// Element source / destination of a level.
+struct Src {
+  const uint64_t* key;
+  const uint32_t* idx;  // nullptr: the original position is implicit
+  int map_f64;          // keys need the float64 order map on load
+};
+struct Dst {
+  uint64_t* key;
+  uint32_t* idx;
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+
+// splitmix64 (Steele, Lea & Flood 2014): output c of the stream at state s.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t c) {
+  uint64_t z = s + (c + 1) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Order map of binary64 bit patterns: negative -> all bits flipped,
+// non-negative -> sign bit flipped.  Its inverse restores the original bits.
+__device__ __forceinline__ uint64_t f64_to_ordered(uint64_t u) {
+  return u ^ ((uint64_t)((int64_t)u >> 63) | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ uint64_t ordered_to_f64(uint64_t o) {
+  return o ^ ((uint64_t)(~((int64_t)o >> 63)) | 0x8000000000000000ULL);
+}
+
+__device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Exclusive block scan of one u64 per thread (NT threads, NT % 32 == 0).
+// sm must hold NT/32 u64.  Returns the exclusive prefix; *total gets the sum.
+template <int NT>
+__device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* total,
+                                                        uint64_t* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t s = (lane < NT / 32) ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NT / 32) sm[lane] = s;
+  }
+  __syncthreads();
+  uint64_t prefix = (w > 0 ? sm[w - 1] : 0) + x - v;
+  *total = sm[NT / 32 - 1];
+  __syncthreads();
+  return prefix;
+}
+
+// In-place bitonic sort of P (a power of two) (key, idx) pairs in shared
+// memory by NT threads; callers pad with (UINT64_MAX, UINT32_MAX).
+template <int NT>
+__device__ __forceinline__ void block_bitonic_sort(uint64_t* sk, uint32_t* si, int P) {
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < (P >> 1); t += NT) {
+        const int lo = 2 * t - (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t a = sk[lo], b = sk[hi];
+        const uint32_t ia = si[lo], ib = si[hi];
+        const bool gt = a > b || (a == b && ia > ib);
+        if (gt == up) {
+          sk[lo] = b; sk[hi] = a;
+          si[lo] = ib; si[hi] = ia;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+__host__ __device__ __forceinline__ int log2_u32(uint32_t p) {  // p a power of two
+  int l = 0;
+  while ((1u << l) < p) ++l;
+  return l;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// Profiling hook owned by the context: CUDA events around every launch.
+struct KernelTimer {
+  void begin(const char* name, cudaStream_t s);
+  void end(cudaStream_t s);
+  void* impl = nullptr;
+};
+
+struct LaunchEnv {
+  cudaStream_t stream;
+  int num_sms;
+  KernelTimer* timer;   // may be null
+  uint64_t* launches;   // launch counter
+};
+
+void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
+                       uint64_t n, uint32_t k1, int direct);
+void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const SegIn* list_in,
+                  SegIn* list_out, LevelSeg* segs, Src src, Dst dst, uint16_t dst_where,
+                  uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,
+                  uint32_t* ssamp_idx, uint32_t* hist, uint32_t* block_sums, FinalItem* items,
+                  int kmax_level, int last_level, int emit_final, uint64_t* offsets_out,
+                  uint64_t n_total, int unmap_out);
+void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
+                       uint64_t item_cap, const uint64_t* in_key, Dst out, Dst tmp, int f64);
+
+}  // namespace rsort

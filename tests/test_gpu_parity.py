@@ -1,0 +1,190 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+The result of every call is unique (ties broken by position), so the CUDA
+output must equal the oracle's bit for bit: keys, permutation, partition
+layout and bucket offsets.  At full size (2^28 keys, the plain-sort workload
+that bench.py times) the oracle cannot sort in test time, so the output is
+checked through properties that determine it uniquely, plus sampled ranks the
+oracle definition gives one element at a time.
+"""
+import numpy as np
+import pytest
+import torch
+
+import instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1606_08766_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(a.view(np.int64).copy()).cuda()
+
+
+def _host_u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def _host_u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+PART_CASES = [("uniform", 64), ("uniform", 37), ("zero", 64), ("deter_dupl", 64),
+              ("rand_dupl", 100), ("staggered", 64), ("gaussian", 64), ("all_to_one", 64),
+              ("mirrored", 16), ("bucket_sorted", 2048), ("g_group", 1), ("reverse", 2)]
+
+
+@pytest.mark.parametrize("name,k", PART_CASES)
+def test_partition_matches_oracle(ctx, oracle_mod, name, k):
+    n = (1 << 17) + 1237  # several chunks plus a ragged tail
+    keys = instances.generate(name, n, p=64, seed=7)
+    ref = oracle_mod.partition(keys, k, seed=5)
+    ko, po, off = ctx.partition(_dev(keys), k, seed=5)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+    np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
+    np.testing.assert_array_equal(_host_u64(ko), ref["keys_out"])
+    ctx.check()
+
+
+def test_partition_f64_matches_oracle(ctx, oracle_mod):
+    keys, _ = instances.segmented_f64(1, 17, seed=3)
+    keys = keys[: 100_000]
+    ref = oracle_mod.partition(keys, 50, seed=9, key_type=oracle_mod.KEY_F64)
+    t = torch.from_numpy(keys.view(np.float64).copy()).cuda()
+    ko, po, off = ctx.partition(t, 50, seed=9)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+    np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint64), ref["keys_out"])
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 4096])
+def test_partition_small_and_empty(ctx, oracle_mod, n):
+    keys = instances.generate("uniform", n, seed=1)
+    ref = oracle_mod.partition(keys, 8, seed=2)
+    ko, po, off = ctx.partition(_dev(keys), 8, seed=2)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+    if n:
+        np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
+
+
+SORT_SIZES = [1, 2, 3, 31, 64, 65, 1000, 4096, 4097, 10_007, (1 << 17) + 3]
+
+
+@pytest.mark.parametrize("n", SORT_SIZES)
+@pytest.mark.parametrize("name", ["uniform", "zero", "rand_dupl", "reverse"])
+def test_sort_matches_oracle_sizes(ctx, oracle_mod, n, name):
+    keys = instances.generate(name, n, p=64, seed=3)
+    rk, rp = oracle_mod.sort(keys)
+    ko, po = ctx.sort(_dev(keys), p=64 if n > 64 else 1, seed=11)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+
+
+@pytest.mark.parametrize("name", instances.NAMES)
+def test_sort_matches_oracle_all_instances(ctx, oracle_mod, name):
+    n = (1 << 20) + 77  # the 2^20, p = 64 workload with a ragged tail
+    keys = instances.generate(name, n, p=64, seed=1)
+    rk, rp = oracle_mod.sort(keys)
+    ko, po = ctx.sort(_dev(keys), p=64, seed=1)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+    ctx.check()
+
+
+@pytest.mark.parametrize("p", [1, 2, 37, 1024, 2048])
+def test_sort_any_p(ctx, oracle_mod, p):
+    keys = instances.generate("gaussian", 300_001, p=max(p, 2), seed=2)
+    rk, rp = oracle_mod.sort(keys)
+    ko, po = ctx.sort(_dev(keys), p=p, seed=3)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+
+
+def test_sort_f64(ctx, oracle_mod):
+    keys, _ = instances.segmented_f64(64, 14, seed=5)
+    x = keys.view(np.float64).copy()
+    assert x.shape[0] > 100_000
+    x[:7] = [-0.0, 0.0, np.inf, -np.inf, -1e-310, 1e-310, 0.0]
+    rk, rp = oracle_mod.sort(x, oracle_mod.KEY_F64)
+    ko, po = ctx.sort(torch.from_numpy(x).cuda(), p=64, seed=1)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint64), rk)
+
+
+def test_sort_in_place_alias(ctx, oracle_mod):
+    keys = instances.generate("uniform", 500_000, seed=4)
+    rk, rp = oracle_mod.sort(keys)
+    t = _dev(keys)
+    ko, po = ctx.sort(t, p=64, keys_out=t)
+    np.testing.assert_array_equal(_host_u64(t), rk)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+
+
+def test_seed_invariance_and_stats(ctx):
+    keys = _dev(instances.generate("deter_dupl", 1 << 20, p=64, seed=1))
+    a, pa, sa = ctx.sort(keys, p=64, seed=1, stats=True)
+    b, pb, sb = ctx.sort(keys, p=64, seed=12345, stats=True)
+    assert torch.equal(a, b) and torch.equal(pa, pb)
+    assert sa.p == 64 and sa.levels >= 1 and sa.max_over_mean < 1.5
+
+
+def test_invalid_arguments(ctx):
+    from paper_1606_08766_gb300 import RsortError
+    t = _dev(instances.generate("uniform", 10))
+    with pytest.raises(RsortError):
+        ctx.sort(t, p=0)
+    with pytest.raises(RsortError):
+        ctx.sort(t, p=4096)
+    with pytest.raises(RsortError):
+        ctx.partition(t, 0)
+
+
+def _check_sorted_permutation(keys_in: torch.Tensor, keys_out: torch.Tensor, perm: torch.Tensor):
+    """Properties that determine the output uniquely: perm is a permutation,
+    keys_out = keys_in[perm], and (key, perm) is strictly increasing."""
+    n = keys_in.numel()
+    p64 = perm.to(torch.int64) & 0xFFFFFFFF
+    seen = torch.zeros(n, dtype=torch.int32, device=perm.device)
+    seen.index_add_(0, p64, torch.ones(n, dtype=torch.int32, device=perm.device))
+    assert bool((seen == 1).all())
+    assert torch.equal(keys_in[p64], keys_out)
+    # unsigned comparison of int64-held bit patterns: flip the sign bit
+    flip = keys_out ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=keys_out.device)
+    a, b = flip[:-1], flip[1:]
+    ok = (a < b) | ((a == b) & (p64[:-1] < p64[1:]))
+    assert bool(ok.all())
+
+
+def _rank_by_definition(keys: np.ndarray, e: int) -> int:
+    """Oracle definition of the output slot of element e: the number of
+    elements lexicographically smaller than (key[e], e)."""
+    x = keys[e]
+    return int(np.count_nonzero(keys < x) + np.count_nonzero(keys[:e] == x))
+
+
+@pytest.mark.parametrize("name", ["uniform", "zero", "rand_dupl", "staggered"])
+def test_full_size_2p28(ctx, name):
+    n = 1 << 28
+    keys = instances.generate(name, n, p=1024, seed=1)
+    t = _dev(keys)
+    ko, po, st = ctx.sort(t, p=1024, seed=1, stats=True)
+    torch.cuda.synchronize()
+    _check_sorted_permutation(t, ko, po)
+    perm = _host_u32(po)
+    rng = np.random.default_rng(0)
+    for e in rng.integers(0, n, size=4):
+        j = _rank_by_definition(keys, int(e))
+        assert int(perm[j]) == int(e)
+    assert st.p == 1024
+    if name in ("uniform", "zero", "rand_dupl"):
+        assert st.max_over_mean < 1.35
+    del t, ko, po
+    torch.cuda.empty_cache()
