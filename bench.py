@@ -184,7 +184,7 @@ def run_rsort(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = N_KEYS
+    n = args.n
     keys_h = instances.generate("uniform", n, p=P_VIRTUAL, seed=1 + rank)
     keys = torch.from_numpy(keys_h.view(np.int64)).to(dev)
     keys_out = torch.empty_like(keys)
@@ -288,7 +288,9 @@ def run_rsort(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "p": P_VIRTUAL,
+            "config": {"workload": WORKLOAD if n == N_KEYS else
+                       f"Uniform uint64 keys, n={n}, p=1024 virtual partitions, seed 1",
+                       "n": n, "p": P_VIRTUAL,
                        "l2": "inputs (2 GiB keys) larger than L2 (129 MB); no flush needed",
                        "max_over_mean": st.max_over_mean, "levels": st.levels},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -305,6 +307,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsort", choices=["rsort", "reference"])
+    ap.add_argument("--n", type=int, default=N_KEYS,
+                    help="keys per GPU (default 2^28; smaller values are for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -116,6 +116,26 @@ rsort_status rsort_sort(rsort_ctx *ctx, rsort_key_type type, const void *d_keys_
                         uint32_t p_virtual, uint64_t seed, void *stream,
                         rsort_stats *opt_stats);
 
+/* Batched segmented sort in one launch sequence: every segment
+ * s = [d_offsets[s], d_offsets[s+1]) of the n keys is sorted on its own, with
+ * segment-LOCAL positions in d_perm_out (the same bytes as sorting that
+ * segment alone with rsort_sort).  All segments share every launch: segments
+ * of at most 4096 keys go straight to the in-shared-memory sort
+ * (rank-by-counting when tiny), larger ones run the robust sample-sort levels
+ * with a per-segment bucket count; the choice by segment size is the paper's
+ * size-dependent algorithm choice (Section 6, Appendix "Parameter Tuning").
+ * d_offsets: device array of num_segments + 1 nondecreasing u64 values with
+ * d_offsets[num_segments] <= n; keys outside the segments are left untouched.
+ * Offsets are checked on the device: a violation skips that segment and is
+ * reported as RSORT_EDEVICE by rsort_check.  d_keys_in must not alias
+ * d_keys_out.  No host synchronisation: once the context's scratch has been
+ * sized by a first call of the same n, the call can be captured in a CUDA
+ * graph.  Errors: EINVAL, ENOMEM, ECUDA (EDEVICE via rsort_check). */
+rsort_status rsort_segmented(rsort_ctx *ctx, rsort_key_type type, const void *d_keys_in,
+                             void *d_keys_out, uint32_t *d_perm_out, uint64_t n,
+                             const uint64_t *d_offsets, uint32_t num_segments, uint64_t seed,
+                             void *stream);
+
 /* Profiling (tracing): when enabled, the library records CUDA events around
  * every kernel it launches on the call's stream.  rsort_phase_times copies up
  * to max entries of {kernel name, accumulated milliseconds, launches} into the

@@ -73,6 +73,7 @@ def load_library(build_if_missing: bool = True):
         "rsort_check": (i32, [vp]),
         "rsort_partition": (i32, [vp, i32, vp, u64, u32, u64, vp, vp, vp, vp]),
         "rsort_sort": (i32, [vp, i32, vp, vp, vp, u64, u32, u64, vp, ctypes.POINTER(_Stats)]),
+        "rsort_segmented": (i32, [vp, i32, vp, vp, vp, u64, vp, u32, u64, vp]),
         "rsort_set_profiling": (i32, [vp, ctypes.c_int]),
         "rsort_phase_times": (i32, [vp, ctypes.POINTER(ctypes.c_char_p),
                                     ctypes.POINTER(ctypes.c_double),
@@ -172,6 +173,25 @@ class Context:
                                     ctypes.c_void_p(d_out), ctypes.c_void_p(d_perm), n, p,
                                     seed & (2**64 - 1), ctypes.c_void_p(stream_handle), None),
                "rsort_sort")
+
+    def segmented(self, keys: torch.Tensor, offsets: torch.Tensor, seed: int = 1, keys_out=None,
+                  perm_out=None, key_type=None, stream=None):
+        """Sorts every segment [offsets[s], offsets[s+1]) on its own; the
+        permutation holds segment-local positions."""
+        _check_keys(keys)
+        if not offsets.is_cuda or offsets.element_size() != 8 or not offsets.is_contiguous():
+            raise ValueError("offsets must be a contiguous CUDA tensor of 8-byte integers")
+        n = keys.numel()
+        if keys_out is None:
+            keys_out = torch.empty_like(keys)
+        if perm_out is None:
+            perm_out = torch.empty(n, dtype=torch.int32, device=keys.device)
+        nseg = max(offsets.numel() - 1, 0)
+        rc = self._lib.rsort_segmented(self._ctx, _key_type(keys, key_type), _ptr(keys),
+                                       _ptr(keys_out), _ptr(perm_out), n, _ptr(offsets), nseg,
+                                       seed & (2**64 - 1), _stream_handle(stream))
+        _check(rc, "rsort_segmented")
+        return keys_out, perm_out
 
     def partition(self, keys: torch.Tensor, k: int, seed: int = 1, key_type=None, stream=None):
         """One robust partition step: (keys_out, positions, offsets[k+1])."""

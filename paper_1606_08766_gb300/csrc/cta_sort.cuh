@@ -1,0 +1,199 @@
+// cta_sort.cuh -- one CTA sorts up to NT*ITEMS (key, position) pairs that its
+// threads hold in registers (element e = r*NT + threadIdx.x sits in slot r).
+//
+// The result is the lexicographic (key, position) order, left in shared
+// memory.  Size-dependent choice (the paper's per-input-size algorithm choice,
+// Section 6, applied to one bucket):
+//
+//   m <= kRankMax       rank-by-counting: slot = #{pairs smaller than me}
+//                       (the ranking of Appendix "Fast Work-Inefficient
+//                       Ranking", all in one CTA)
+//   otherwise           split the bucket's key range [min, max] into ~2m
+//                       equal-width bins (a counting sort in shared memory),
+//                       then rank-by-counting inside each bin; the bins of a
+//                       bucket are tiny unless its keys cluster
+//   a crowded bin       bitonic sort of the whole bucket (Appendix "Bitonic
+//   (> kBinLimit)       Sort"), which needs no assumption on the keys
+//
+// A bucket whose keys are all equal and whose elements arrive in position
+// order (every bucket produced by the stable scatter) is already sorted.
+#pragma once
+
+#include "rsort_internal.cuh"
+
+namespace rsort {
+
+constexpr int kBinLimit = 32;
+static_assert(kRankMax <= kLocalThreads, "rank-by-counting holds one element per thread");
+
+struct CtaSortSmem {
+  uint64_t* k;     // [cap]      cap = NT * ITEMS
+  uint32_t* i;     // [cap]
+  uint32_t* hist;  // [cap]      2*cap 16-bit bin counters, packed in pairs
+};
+
+template <int NT>
+__device__ __forceinline__ void block_minmax_u64(uint64_t& mn, uint64_t& mx, uint64_t* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t a = __shfl_xor_sync(0xffffffffu, mn, o);
+    const uint64_t b = __shfl_xor_sync(0xffffffffu, mx, o);
+    mn = a < mn ? a : mn;
+    mx = b > mx ? b : mx;
+  }
+  if (lane == 0) {
+    red[2 * w] = mn;
+    red[2 * w + 1] = mx;
+  }
+  __syncthreads();
+  mn = red[0];
+  mx = red[1];
+#pragma unroll
+  for (int q = 1; q < NT / 32; ++q) {
+    mn = red[2 * q] < mn ? red[2 * q] : mn;
+    mx = red[2 * q + 1] > mx ? red[2 * q + 1] : mx;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t bin_start(const uint32_t* hist, uint32_t b) {
+  return (hist[b >> 1] >> ((b & 1) << 4)) & 0xffffu;
+}
+
+// Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
+// in_position_order: the elements arrive with increasing positions.
+template <int NT, int ITEMS>
+__device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], uint32_t m,
+                               bool in_position_order, const CtaSortSmem& s, uint64_t* red,
+                               uint64_t* scan_sm) {
+  constexpr uint32_t kCap = NT * ITEMS;
+  const uint32_t tid = threadIdx.x;
+  if (m <= (uint32_t)kRankMax) {
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const uint32_t e = r * NT + tid;
+      if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
+    }
+    __syncthreads();
+    uint32_t rank = 0;
+    if (tid < m) {
+      for (uint32_t q = 0; q < m; ++q) rank += pair_less(s.k[q], s.i[q], key[0], idx[0]) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (tid < m) { s.k[rank] = key[0]; s.i[rank] = idx[0]; }
+    __syncthreads();
+    return;
+  }
+  uint64_t mn = ~0ULL, mx = 0;
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) {
+      mn = key[r] < mn ? key[r] : mn;
+      mx = key[r] > mx ? key[r] : mx;
+    }
+  }
+  block_minmax_u64<NT>(mn, mx, red);
+  if (mn == mx && in_position_order) {
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const uint32_t e = r * NT + tid;
+      if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
+    }
+    __syncthreads();
+    return;
+  }
+  // equal-width bins over [mn, mx]
+  const uint32_t nb = 2 * next_pow2_u32(m);  // <= 2 * kCap
+  const int lognb = log2_u32(nb);
+  const uint64_t range = mx - mn;
+  const int bits = range ? 64 - __clzll((long long)range) : 0;
+  const int shift = bits > lognb ? bits - lognb : 0;
+  for (uint32_t w = tid; w < nb / 2; w += NT) s.hist[w] = 0;
+  __syncthreads();
+  uint32_t bs[ITEMS];
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) {
+      const uint32_t b = (uint32_t)((key[r] - mn) >> shift);
+      const uint32_t sh = (b & 1) << 4;
+      const uint32_t old = atomicAdd(&s.hist[b >> 1], 1u << sh);
+      bs[r] = (b << 16) | ((old >> sh) & 0xffffu);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the nb 16-bit counters (nb/2 words; each thread a run)
+  {
+    const uint32_t words = nb / 2;
+    const uint32_t per = (words + NT - 1) / NT;
+    const uint32_t w0 = tid * per;
+    uint32_t loc = 0;
+    for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
+      const uint32_t v = s.hist[w];
+      loc += (v & 0xffffu) + (v >> 16);
+    }
+    uint64_t tot;
+    uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
+    for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
+      const uint32_t v = s.hist[w];
+      const uint32_t lo = run, hi = run + (v & 0xffffu);
+      s.hist[w] = lo | (hi << 16);
+      run = hi + (v >> 16);
+    }
+  }
+  __syncthreads();
+  bool crowded = false;
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) {
+      const uint32_t b = bs[r] >> 16;
+      const uint32_t lo = bin_start(s.hist, b);
+      const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
+      crowded |= (hi - lo) > (uint32_t)kBinLimit;
+    }
+  }
+  if (__syncthreads_or(crowded)) {
+    // clustered keys: bitonic sort of the whole bucket
+    const uint32_t P = next_pow2_u32(m);
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      const uint32_t e = r * NT + tid;
+      if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
+    }
+    for (uint32_t e = m + tid; e < P; e += NT) { s.k[e] = ~0ULL; s.i[e] = ~0u; }
+    block_bitonic_sort<NT>(s.k, s.i, (int)P);
+    return;
+  }
+  // counting-sort scatter into the bins
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) {
+      const uint32_t p = bin_start(s.hist, bs[r] >> 16) + (bs[r] & 0xffffu);
+      s.k[p] = key[r];
+      s.i[p] = idx[r];
+    }
+  }
+  __syncthreads();
+  // rank by counting inside each bin
+  uint32_t fin[ITEMS];
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) {
+      const uint32_t b = bs[r] >> 16;
+      const uint32_t lo = bin_start(s.hist, b);
+      const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
+      uint32_t rank = 0;
+      for (uint32_t q = lo; q < hi; ++q) rank += pair_less(s.k[q], s.i[q], key[r], idx[r]) ? 1u : 0u;
+      fin[r] = lo + rank;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    if (r * NT + tid < m) { s.k[fin[r]] = key[r]; s.i[fin[r]] = idx[r]; }
+  }
+  __syncthreads();
+  (void)kCap;
+}
+
+}  // namespace rsort

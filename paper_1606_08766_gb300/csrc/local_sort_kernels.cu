@@ -4,17 +4,15 @@
 //
 //   size 1 or equality bucket  copy through (the stable scatter already left
 //                              the elements in position order)
-//   size <= kRankMax           rank-by-counting: an element's output slot is
-//                              the number of elements lexicographically
-//                              smaller than it (the ranking of Appendix
-//                              "Fast Work-Inefficient Ranking" inside one CTA)
-//   size <= kBucketCap         bitonic sort in shared memory (Appendix
-//                              "Bitonic Sort"), padded to a power of two
+//   size <= kBucketCap         cta_sort_pairs (cta_sort.cuh): rank-by-counting
+//                              for tiny buckets, equal-width bins + rank-by-
+//                              counting for the rest, bitonic when keys cluster
 //   larger (only after the     merge sort through global memory by one CTA:
 //   last partition level)      bitonic-sorted runs, then pairwise merges
 //
 // Buckets are taken from a device work list with an atomic cursor by a
 // persistent grid.  The final store restores float64 bit patterns.
+#include "cta_sort.cuh"
 #include "rsort_internal.cuh"
 
 namespace rsort {
@@ -139,10 +137,15 @@ __device__ void sort_big(const Bufs& B, const FinalItem& f, uint64_t* sk, uint32
 
 __global__ void __launch_bounds__(kLocalThreads)
 k_local_sort(DevState* st, const FinalItem* items, uint64_t item_cap, Bufs B) {
-  constexpr int NT = kLocalThreads;
+  constexpr int NT = kLocalThreads, IT = kLocalItems;
+  static_assert(NT * IT == kBucketCap, "one CTA holds one whole bucket");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* sk = (uint64_t*)smem_raw;                  // [kBucketCap]
-  uint32_t* si = (uint32_t*)(sk + kBucketCap);         // [kBucketCap]
+  CtaSortSmem s;
+  s.k = (uint64_t*)smem_raw;                // [kBucketCap]
+  s.i = (uint32_t*)(s.k + kBucketCap);      // [kBucketCap]
+  s.hist = s.i + kBucketCap;                // [kBucketCap]
+  __shared__ uint64_t red[2 * NT / 32];
+  __shared__ uint64_t scan_sm[NT / 32];
   __shared__ uint32_t s_item;
   const uint64_t nitems = umin64(st->nfinal, item_cap);
   for (;;) {
@@ -163,38 +166,28 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t item_cap, Bufs B) {
       continue;
     }
     if (f.kind == kKindBig) {
-      sort_big(B, f, sk, si);
+      sort_big(B, f, s.k, s.i);
       continue;
     }
-    if (m <= (uint32_t)kRankMax) {
-      for (uint32_t t = threadIdx.x; t < m; t += NT) load_elem(B, f, t, sk[t], si[t]);
-      __syncthreads();
-      if (threadIdx.x < m) {
-        const uint64_t mk = sk[threadIdx.x];
-        const uint32_t mi = si[threadIdx.x];
-        uint32_t rank = 0;
-        for (uint32_t q = 0; q < m; ++q) rank += pair_less(sk[q], si[q], mk, mi) ? 1u : 0u;
-        store_out(B, f.start + rank, mk, mi);
-      }
-      __syncthreads();
-      continue;
+    uint64_t key[IT];
+    uint32_t idx[IT];
+#pragma unroll
+    for (int r = 0; r < IT; ++r) {
+      const uint32_t e = r * NT + threadIdx.x;
+      if (e < m) load_elem(B, f, e, key[r], idx[r]);
     }
-    const int P = (int)next_pow2_u32(m);
-    for (int t = threadIdx.x; t < P; t += NT) {
-      if ((uint32_t)t < m) {
-        load_elem(B, f, t, sk[t], si[t]);
-      } else {
-        sk[t] = ~0ULL;
-        si[t] = ~0u;
-      }
-    }
-    block_bitonic_sort<NT>(sk, si, P);
-    for (uint32_t t = threadIdx.x; t < m; t += NT) store_out(B, f.start + t, sk[t], si[t]);
+    cta_sort_pairs<NT, IT>(key, idx, m, true, s, red, scan_sm);
+    for (uint32_t t = threadIdx.x; t < m; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
     __syncthreads();
   }
 }
 
 }  // namespace
+
+void set_local_kernel_attributes() {
+  cudaFuncSetAttribute(k_local_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kBucketCap * (8 + 4 + 4));
+}
 
 void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
                        uint64_t item_cap, const uint64_t* in_key, Dst out, Dst tmp, int f64) {
@@ -203,10 +196,9 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   B.out = out;
   B.tmp = tmp;
   B.f64 = f64;
-  const int smem = kBucketCap * (8 + 4);
-  cudaFuncSetAttribute(k_local_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = kBucketCap * (8 + 4 + 4);
   Scope sc(e, "local_sort");
-  k_local_sort<<<e.num_sms * 4, kLocalThreads, smem, e.stream>>>(st, items, item_cap, B);
+  k_local_sort<<<e.num_sms * 3, kLocalThreads, smem, e.stream>>>(st, items, item_cap, B);
 }
 
 }  // namespace rsort

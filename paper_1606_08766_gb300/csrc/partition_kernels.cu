@@ -13,6 +13,7 @@
 // the paper's sample sort becomes the scan + scatter through HBM.
 #include <cstdio>
 
+#include "cta_sort.cuh"
 #include "rsort_internal.cuh"
 
 namespace rsort {
@@ -94,25 +95,45 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
 }
 
 // Bucket of element (x, i): the number of splitters lexicographically smaller
-// than (x, i).  The tree descent counts the splitters whose key is smaller
-// than x; if x equals the key of the bounding splitter, the search is repeated
-// on the run of equal splitter keys with positions as tie-breakers.
-template <typename PosFn>
-__device__ __forceinline__ uint32_t classify(uint64_t x, PosFn pos_of, const Splitters& sp) {
-  uint32_t j = 1;
-  for (int l = 0; l < sp.logK; ++l) j = 2 * j + (x > sp.tree[j] ? 1u : 0u);
-  uint32_t b = j - (1u << sp.logK);
-  if (b < sp.nspl && sp.key[b] == x) {
-    // the key equals the bounding splitter's key: break the tie by position
-    const uint32_t i = pos_of();
-    uint32_t lo = b, hi = sp.nspl;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (sp.key[mid] == x && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
-    }
-    b = lo;
+// than (x, i).  R elements descend the tree level by level together (R
+// independent shared-memory loads in flight per level).  The descent counts
+// the splitters whose key is smaller than x and remembers the key of the last
+// node where it turned left, which is the bounding splitter's key; only if x
+// equals it is the search repeated on the run of equal splitter keys with
+// positions as tie-breakers (pos_of(r) is evaluated only then).
+template <int R, typename PosFn>
+__device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t (&b)[R],
+                                               PosFn pos_of, const Splitters& sp) {
+  uint32_t j[R];
+  uint64_t ub[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    j[r] = 1;
+    ub[r] = ~0ULL;
   }
-  return b;
+  for (int l = 0; l < sp.logK; ++l) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint64_t t = sp.tree[j[r]];
+      const bool right = x[r] > t;
+      j[r] = 2 * j[r] + (right ? 1u : 0u);
+      ub[r] = right ? ub[r] : t;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    uint32_t bb = j[r] - (1u << sp.logK);
+    if (bb < sp.nspl && ub[r] == x[r]) {
+      const uint32_t i = pos_of(r);
+      uint32_t lo = bb, hi = sp.nspl;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sp.key[mid] == x[r] && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
+      }
+      bb = lo;
+    }
+    b[r] = bb;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -270,13 +291,20 @@ k_sample(const DevState* st, const LevelSeg* segs, Src src, uint64_t* samp_key,
   }
 }
 
-// Step 2a: sort chunks of up to kSampleChunk sample pairs in shared memory.
-// Single-chunk samples go straight to the sorted-sample array.
-__global__ void __launch_bounds__(512)
+// Step 2a: sort chunks of up to kSampleChunk sample pairs in one CTA each
+// (cta_sort_pairs).  Single-chunk samples go straight to the sorted-sample
+// array.  Samples of a segment are drawn in position order.
+__global__ void __launch_bounds__(kLocalThreads)
 k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_key,
                      uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
-  __shared__ uint64_t sk[kSampleChunk];
-  __shared__ uint32_t si[kSampleChunk];
+  constexpr int NT = kLocalThreads, IT = kSampleChunk / kLocalThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CtaSortSmem s;
+  s.k = (uint64_t*)smem_raw;
+  s.i = (uint32_t*)(s.k + kSampleChunk);
+  s.hist = s.i + kSampleChunk;
+  __shared__ uint64_t red[2 * NT / 32];
+  __shared__ uint64_t scan_sm[NT / 32];
   const uint64_t total = st->total_schunks;
   const uint32_t G = st->cur_nseg;
   for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
@@ -284,23 +312,23 @@ k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_ke
     const LevelSeg sg = segs[g];
     const uint64_t cl = c - sg.schunk_off;
     const uint64_t base = sg.samp_off + cl * kSampleChunk;
-    const int len = (int)umin64(kSampleChunk, sg.S - cl * kSampleChunk);
-    const int P = (int)next_pow2_u32((uint32_t)len);
-    for (int t = threadIdx.x; t < P; t += 512) {
-      if (t < len) {
-        sk[t] = samp_key[base + t];
-        si[t] = samp_idx[base + t];
-      } else {
-        sk[t] = ~0ULL;
-        si[t] = ~0u;
+    const uint32_t len = (uint32_t)umin64(kSampleChunk, sg.S - cl * kSampleChunk);
+    uint64_t key[IT];
+    uint32_t idx[IT];
+#pragma unroll
+    for (int r = 0; r < IT; ++r) {
+      const uint32_t e = r * NT + threadIdx.x;
+      if (e < len) {
+        key[r] = samp_key[base + e];
+        idx[r] = samp_idx[base + e];
       }
     }
-    block_bitonic_sort<512>(sk, si, P);
+    cta_sort_pairs<NT, IT>(key, idx, len, true, s, red, scan_sm);
     uint64_t* ok = sg.nschunks == 1 ? ssamp_key : samp_key;
     uint32_t* oi = sg.nschunks == 1 ? ssamp_idx : samp_idx;
-    for (int t = threadIdx.x; t < len; t += 512) {
-      ok[base + t] = sk[t];
-      oi[base + t] = si[t];
+    for (uint32_t t = threadIdx.x; t < len; t += NT) {
+      ok[base + t] = s.k[t];
+      oi[base + t] = s.i[t];
     }
     __syncthreads();
   }
@@ -423,14 +451,16 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
         const uint64_t pos = base + r * 32 + lane;
         key[r] = pos < ce ? load_key(src, pos) : 0;
       }
+      uint32_t bk[kItems];
+      // positions are read only when a key ties with a splitter key
+      classify_batch<kItems>(key, bk, [&](int r) {
+        const uint64_t pos = base + r * 32 + lane;
+        return pos < ce ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0u;
+      }, sm.sp);
 #pragma unroll
       for (int r = 0; r < kItems; ++r) {
-        const uint64_t pos = base + r * 32 + lane;
-        const bool v = pos < ce;
-        // positions are read only when a key ties with a splitter key
-        const uint32_t b = classify(key[r], [&] {
-          return v ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0u;
-        }, sm.sp);
+        const bool v = base + r * 32 + lane < ce;
+        const uint32_t b = bk[r];
         const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
         if (__all_sync(0xffffffffu, v && b == b0)) {
           if (lane == 0) atomicAdd(&sm.hist[b0], 32u);
@@ -550,11 +580,12 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       }
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
+      classify_batch<kItems>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
 #pragma unroll
       for (int r = 0; r < kItems; ++r) {
         const uint64_t pos = wbase + r * 32 + lane;
         const bool v = pos < ce;
-        const uint32_t b = v ? classify(key[r], [&] { return idx[r]; }, sm.sp) : 0xffffffffu;
+        const uint32_t b = v ? bk[r] : 0xffffffffu;
         bk[r] = b;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         const uint32_t c0 = v ? my_cnt[b] : 0;
@@ -691,6 +722,63 @@ void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem
 
 size_t part_smem_bytes_host(uint32_t kmax, bool scatter) { return part_smem_bytes(kmax, scatter); }
 
+void set_partition_kernel_attributes() {
+  cudaFuncSetAttribute(k_sample_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kSampleChunk * (8 + 4 + 4));
+  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)part_smem_bytes(kMaxK, false));
+  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)part_smem_bytes(kMaxK, true));
+}
+
+// Segmented input: every segment [offsets[s], offsets[s+1]) is checked and
+// routed by size: empty ones are skipped, those that fit one CTA go straight
+// to the in-SM sort (original positions relative to the segment start), the
+// rest become level-1 segments of the sample sort.  Bad offsets raise a
+// device error flag instead of being followed.
+__global__ void __launch_bounds__(256)
+k_init_segments(DevState* st, const uint64_t* offsets, uint32_t nseg, uint64_t n,
+                SegIn* list_l1, FinalItem* items, uint64_t seg_cap, uint64_t final_cap) {
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg;
+       s += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = offsets[s], b = offsets[s + 1];
+    if (b < a || b > n || (b - a) > 0xFFFFFFFFull) {
+      atomicOr(&st->error, kErrBadOffsets);
+      continue;
+    }
+    const uint64_t m = b - a;
+    if (m == 0) continue;
+    if (m <= (uint64_t)kBucketCap) {
+      FinalItem f;
+      f.start = a;
+      f.idx_base = a;
+      f.size = (uint32_t)m;
+      f.where = kWhereInput;
+      f.kind = m == 1 ? kKindCopy : kKindSort;
+      const uint32_t slot = atomicAdd(&st->nfinal, 1u);
+      if (slot < final_cap) items[slot] = f;
+      else atomicOr(&st->error, kErrFinalCap);
+    } else {
+      SegIn in;
+      in.start = a;
+      in.m = (uint32_t)m;
+      in.k_hint = 0;
+      const uint32_t slot = atomicAdd(&st->nseg[1], 1u);
+      if (slot < seg_cap) list_l1[slot] = in;
+      else atomicOr(&st->error, kErrSegCap);
+    }
+  }
+}
+
+void launch_init_segments(const LaunchEnv& e, DevState* st, const uint64_t* offsets,
+                          uint32_t nseg, uint64_t n, SegIn* list_l1, FinalItem* items,
+                          uint64_t seg_cap, uint64_t final_cap) {
+  Scope sc(e, "init_segments");
+  const int grid = (int)umin64((nseg + 255) / 256 + 1, (uint64_t)e.num_sms * 8);
+  k_init_segments<<<grid, 256, 0, e.stream>>>(st, offsets, nseg, n, list_l1, items, seg_cap,
+                                              final_cap);
+}
+
 void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const SegIn* list_in,
                   SegIn* list_out, LevelSeg* segs, Src src, Dst dst, uint16_t dst_where,
                   uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,
@@ -721,7 +809,8 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   {
     Scope sc(e, nm[2]);
-    k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms * 2), 512, 0, e.stream>>>(
+    const int smem = kSampleChunk * (8 + 4 + 4);
+    k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms * 3), kLocalThreads, smem, e.stream>>>(
         st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
   }
   {
@@ -731,10 +820,6 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false);
   const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true);
-  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)part_smem_bytes(kMaxK, false));
-  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)part_smem_bytes(kMaxK, true));
   const int part_grid = grid_for(P.chunk_cap, 1, sms * 2);
   {
     Scope sc(e, nm[4]);

@@ -5,6 +5,7 @@
 // every step of the method runs in the kernels of partition_kernels.cu and
 // local_sort_kernels.cu.  Nothing here synchronises unless a caller asks for
 // a read-back (stats, rsort_check, phase times).
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -264,6 +265,47 @@ T* at(rsort_ctx* c, size_t off) {
   return reinterpret_cast<T*>(static_cast<unsigned char*>(c->arena) + off);
 }
 
+// Kernel attributes (dynamic shared memory limits) are set once per device,
+// outside any stream capture.
+void set_attributes_once(int device) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == device) return;
+  set_partition_kernel_attributes();
+  set_local_kernel_attributes();
+  done.push_back(device);
+}
+
+// Enqueues the partition levels and the in-SM sort after the level-1 list and
+// the directly sortable items have been initialised.
+void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, DevState* st,
+                              FinalItem* items, SegIn* const lists[2], rsort_key_type type,
+                              const void* d_keys_in, const Dst& out, const Dst& tmp,
+                              uint64_t seed, uint32_t k1) {
+  for (int L = 1; L <= p.levels; ++L) {
+    LevelParams P = level_params(p, L, seed);
+    Src src;
+    if (L == 1) {
+      src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
+    } else {
+      const Dst& prev = ((L - 1) & 1) ? tmp : out;
+      src = Src{prev.key, prev.idx, 0};
+    }
+    const Dst& dst = (L & 1) ? tmp : out;
+    const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
+    const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
+    launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(c, p.off_segs), src,
+                 dst, where, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
+                 at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
+                 at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums), items, kmax,
+                 L == p.levels, 1, nullptr, p.n, 0);
+  }
+  launch_local_sort(e, st, items, p.final_cap, (const uint64_t*)d_keys_in, out, tmp,
+                    type == RSORT_KEY_F64);
+}
+
 LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   LaunchEnv e;
   e.stream = s;
@@ -312,6 +354,7 @@ rsort_status rsort_create(rsort_ctx** out, int device, uint64_t hbm_budget_bytes
   c->budget = hbm_budget_bytes;
   DeviceGuard g(device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  set_attributes_once(device);
   if (cudaMallocHost(&c->h_state, sizeof(DevState)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -343,10 +386,14 @@ rsort_status rsort_check(rsort_ctx* c) {
   cuda_status(c);
   if (c->arena) {
     DevState st;
-    if (cudaMemcpy(&st, c->arena, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(&st, c->arena, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) {
       latch(c, RSORT_ECUDA);
-    else if (st.error)
+    } else if (st.error) {
       latch(c, RSORT_EDEVICE);
+      // the error is reported once: clear the device word
+      cudaMemset(static_cast<unsigned char*>(c->arena) + offsetof(DevState, error), 0,
+                 sizeof(uint32_t));
+    }
   }
   rsort_status s = c->latched;
   c->latched = RSORT_OK;
@@ -438,28 +485,8 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
   launch_init_plain(e, st, lists[1], items, n, k1, direct);
   Dst out{(uint64_t*)d_keys_out, d_perm_out};
   Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
-  if (!direct) {
-    for (int L = 1; L <= p.levels; ++L) {
-      LevelParams P = level_params(p, L, seed);
-      Src src;
-      if (L == 1) {
-        src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
-      } else {
-        const Dst& prev = ((L - 1) & 1) ? tmp : out;
-        src = Src{prev.key, prev.idx, 0};
-      }
-      const Dst& dst = (L & 1) ? tmp : out;
-      const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
-      const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
-      launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(c, p.off_segs), src,
-                   dst, where, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
-                   at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
-                   at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums), items, kmax,
-                   L == p.levels, 1, nullptr, n, 0);
-    }
-  }
-  launch_local_sort(e, st, items, p.final_cap, (const uint64_t*)d_keys_in, out, tmp,
-                    type == RSORT_KEY_F64);
+  if (direct) p.levels = 0;
+  enqueue_levels_and_local(c, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, k1);
   rs = cuda_status(c);
   if (rs != RSORT_OK) return rs;
   if (opt_stats) {
@@ -487,6 +514,45 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
     if (h.error) return latch(c, RSORT_EDEVICE);
   }
   return RSORT_OK;
+}
+
+rsort_status rsort_segmented(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                             void* d_keys_out, uint32_t* d_perm_out, uint64_t n,
+                             const uint64_t* d_offsets, uint32_t num_segments, uint64_t seed,
+                             void* stream) {
+  if (!c || (type != RSORT_KEY_U64 && type != RSORT_KEY_F64)) return RSORT_EINVAL;
+  if (n > 0xFFFFFFFFull) return RSORT_EINVAL;
+  if (num_segments > 0 && !d_offsets) return RSORT_EINVAL;
+  if (n > 0 && (!d_keys_in || !d_keys_out || !d_perm_out)) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->latched != RSORT_OK) {
+    rsort_status s = c->latched;
+    c->latched = RSORT_OK;
+    return s;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (n == 0 || num_segments == 0) return RSORT_OK;
+  LaunchEnv e = env_of(c, s);
+  Plan p;
+  const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
+  plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
+  p.final_cap += num_segments;
+  p.need_tmp = true;
+  layout(p);
+  rsort_status rs = ensure_arena(c, p.total, s);
+  if (rs != RSORT_OK) return latch(c, rs);
+  DevState* st = at<DevState>(c, p.off_state);
+  FinalItem* items = at<FinalItem>(c, p.off_items);
+  SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
+  launch_init_plain(e, st, lists[1], items, 0, 0, 0);  // reset the control block
+  launch_init_segments(e, st, d_offsets, num_segments, n, lists[1], items, p.seg_cap,
+                       p.final_cap);
+  Dst out{(uint64_t*)d_keys_out, d_perm_out};
+  Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
+  enqueue_levels_and_local(c, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, 0);
+  return cuda_status(c);
 }
 
 rsort_status rsort_set_profiling(rsort_ctx* c, int enable) {

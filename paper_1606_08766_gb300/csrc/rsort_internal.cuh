@@ -24,7 +24,8 @@ constexpr int kTargetBucket = 1024;               // aim for this final bucket s
 constexpr int kSampleChunk = 4096;                // sample sort: pairs per CTA chunk
 constexpr int kDeepOversample = 16;               // samples per bucket at levels >= 2
 constexpr int kMaxLevels = 3;                     // partition levels before fallback
-constexpr int kLocalThreads = 512;                // in-SM bucket sort CTA
+constexpr int kLocalThreads = 256;                // in-SM bucket sort CTA
+constexpr int kLocalItems = 16;                   // kLocalThreads * kLocalItems = kBucketCap
 constexpr int kRankMax = 64;                      // rank-by-counting up to this size
 constexpr int kScanTile = 4096;                   // device scan tile (1024 x 4)
 
@@ -93,6 +94,7 @@ enum : uint32_t {
   kErrFinalCap = 1u << 4,
   kErrSchunkCap = 1u << 5,
   kErrBucketCap = 1u << 6,
+  kErrBadOffsets = 1u << 7,
 };
 
 // Parameters of one level, fixed on the host.
@@ -239,6 +241,11 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
                   uint32_t* ssamp_idx, uint32_t* hist, uint32_t* block_sums, FinalItem* items,
                   int kmax_level, int last_level, int emit_final, uint64_t* offsets_out,
                   uint64_t n_total, int unmap_out);
+void launch_init_segments(const LaunchEnv& e, DevState* st, const uint64_t* offsets,
+                          uint32_t nseg, uint64_t n, SegIn* list_l1, FinalItem* items,
+                          uint64_t seg_cap, uint64_t final_cap);
+void set_partition_kernel_attributes();
+void set_local_kernel_attributes();
 void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
                        uint64_t item_cap, const uint64_t* in_key, Dst out, Dst tmp, int f64);
 
