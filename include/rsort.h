@@ -136,6 +136,28 @@ rsort_status rsort_segmented(rsort_ctx *ctx, rsort_key_type type, const void *d_
                              const uint64_t *d_offsets, uint32_t num_segments, uint64_t seed,
                              void *stream);
 
+/* Allocation-free variant of rsort_partition (the paper has no counterpart;
+ * this is a library-level convenience).  It exists for callers that cannot
+ * allocate device memory at the moment they partition: code running while a
+ * CUDA graph is captured in a strict capture mode, frameworks whose device
+ * memory must all come from their own allocator, and real-time loops that
+ * forbid allocation after start-up.  It needs no context.
+ *   - Same arguments, result and errors as rsort_partition (caller-owned
+ *     inputs and outputs), on the CURRENT device and the given stream.
+ *   - Scratch comes from one fixed 8 MiB device array inside librsort that
+ *     every GPU loading the library holds until the process exits.  Limit:
+ *     k <= 1024 (any n <= 2^32 - 1); larger k returns RSORT_EINVAL.
+ *   - The first call on a device looks up that array's device address and
+ *     sets kernel attributes; make that first call before any stream capture.
+ *   - Every call uses the same array (its contents persist between calls and
+ *     are re-initialised by each call), so calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine. */
+rsort_status rsort_partition_noalloc(rsort_key_type type, const void *d_keys_in, uint64_t n,
+                                     uint32_t k, uint64_t seed, void *d_keys_out,
+                                     uint32_t *d_pos_out, uint64_t *d_offsets_out,
+                                     void *stream);
+
 /* Profiling (tracing): when enabled, the library records CUDA events around
  * every kernel it launches on the call's stream.  rsort_phase_times copies up
  * to max entries of {kernel name, accumulated milliseconds, launches} into the

@@ -7,7 +7,7 @@ behind the C ABI declared in ``include/rsort.h``; this package only marshals
 arguments (PyTorch supplies device memory and streams).
 """
 from .binding import (KEY_F64, KEY_U64, Context, RsortError, Stats, library_path,
-                      load_library)
+                      load_library, partition_noalloc)
 
 __all__ = ["Context", "RsortError", "Stats", "KEY_U64", "KEY_F64", "load_library",
-           "library_path"]
+           "library_path", "partition_noalloc"]

@@ -74,6 +74,7 @@ def load_library(build_if_missing: bool = True):
         "rsort_partition": (i32, [vp, i32, vp, u64, u32, u64, vp, vp, vp, vp]),
         "rsort_sort": (i32, [vp, i32, vp, vp, vp, u64, u32, u64, vp, ctypes.POINTER(_Stats)]),
         "rsort_segmented": (i32, [vp, i32, vp, vp, vp, u64, vp, u32, u64, vp]),
+        "rsort_partition_noalloc": (i32, [i32, vp, u64, u32, u64, vp, vp, vp, vp]),
         "rsort_set_profiling": (i32, [vp, ctypes.c_int]),
         "rsort_phase_times": (i32, [vp, ctypes.POINTER(ctypes.c_char_p),
                                     ctypes.POINTER(ctypes.c_double),
@@ -114,6 +115,25 @@ def _check_keys(t: torch.Tensor):
         raise ValueError("keys must be a CUDA tensor")
     if t.element_size() != 8 or not t.is_contiguous() or t.dim() != 1:
         raise ValueError("keys must be a contiguous 1-D tensor of 8-byte elements")
+
+
+def partition_noalloc(keys: torch.Tensor, k: int, seed: int, keys_out: torch.Tensor,
+                      pos_out: torch.Tensor, offsets_out: torch.Tensor, key_type=None, stream=None):
+    """Allocation-free partition step on the current device.
+
+    For callers that cannot allocate device memory when they partition; the
+    outputs must be supplied (keys_out like keys, pos_out int32[n],
+    offsets_out int64[k + 1]) and the scratch is librsort's fixed static
+    array.  Calls that overlap on the GPU race on that array."""
+    lib = load_library()
+    _check_keys(keys)
+    n = keys.numel()
+    if keys_out.numel() != n or pos_out.numel() != n or offsets_out.numel() != k + 1:
+        raise ValueError("output sizes do not match n and k")
+    rc = lib.rsort_partition_noalloc(_key_type(keys, key_type), _ptr(keys), n, k,
+                                     seed & (2**64 - 1), _ptr(keys_out), _ptr(pos_out),
+                                     _ptr(offsets_out), _stream_handle(stream))
+    _check(rc, "rsort_partition_noalloc")
 
 
 class Context:
