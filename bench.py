@@ -190,6 +190,11 @@ def run_rsort(args):
     keys_out = torch.empty_like(keys)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     ctx = Context(local)
+    tunables = {}
+    for kv in args.tunable:
+        name, val = kv.split("=", 1)
+        ctx.set_tunable(name, int(val))
+        tunables[name] = int(val)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
 
@@ -292,7 +297,8 @@ def run_rsort(args):
                        f"Uniform uint64 keys, n={n}, p=1024 virtual partitions, seed 1",
                        "n": n, "p": P_VIRTUAL,
                        "l2": "inputs (2 GiB keys) larger than L2 (129 MB); no flush needed",
-                       "max_over_mean": st.max_over_mean, "levels": st.levels},
+                       "max_over_mean": st.max_over_mean, "levels": st.levels,
+                       "tunables": {"classifier": ctx.get_tunable("classifier")}},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches, "kernels": kernels,
         }))
@@ -307,6 +313,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsort", choices=["rsort", "reference"])
+    ap.add_argument("--tunable", action="append", default=[],
+                    help="name=value tunable of the library context (repeatable)")
     ap.add_argument("--n", type=int, default=N_KEYS,
                     help="keys per GPU (default 2^28; smaller values are for profiling)")
     args = ap.parse_args()

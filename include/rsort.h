@@ -167,6 +167,16 @@ rsort_status rsort_set_profiling(rsort_ctx *ctx, int enable);
 rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
                                uint64_t *launches, int max, int *count);
 
+/* Tunables of a context (also settable from the tune table file given to
+ * rsort_create, one "name value" per line).  They change speed, never
+ * results.
+ *   classifier   0: the splitter tree of Super Scalar Sample Sort (default);
+ *                1: a lookup table over the keys' leading bits into the same
+ *                sorted splitters, then a binary search inside the bin.
+ * Errors: EINVAL for an unknown name or an out-of-range value. */
+rsort_status rsort_set_tunable(rsort_ctx *ctx, const char *name, int64_t value);
+rsort_status rsort_get_tunable(rsort_ctx *ctx, const char *name, int64_t *value);
+
 /* Number of kernels this context has launched since creation. */
 rsort_status rsort_launch_count(rsort_ctx *ctx, uint64_t *out);
 

@@ -81,6 +81,8 @@ def load_library(build_if_missing: bool = True):
                                     ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int)]),
         "rsort_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
+        "rsort_set_tunable": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
+        "rsort_get_tunable": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +244,15 @@ class Context:
         _check(self._lib.rsort_phase_times(self._ctx, names, ms, cnt, cap, ctypes.byref(count)),
                "rsort_phase_times")
         return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(min(cap, count.value))}
+
+    def set_tunable(self, name: str, value: int):
+        _check(self._lib.rsort_set_tunable(self._ctx, name.encode(), value), "rsort_set_tunable")
+
+    def get_tunable(self, name: str) -> int:
+        v = ctypes.c_int64()
+        _check(self._lib.rsort_get_tunable(self._ctx, name.encode(), ctypes.byref(v)),
+               "rsort_get_tunable")
+        return v.value
 
     def launch_count(self) -> int:
         v = ctypes.c_uint64()

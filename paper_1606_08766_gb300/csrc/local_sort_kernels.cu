@@ -135,58 +135,103 @@ __device__ void sort_big(const Bufs& B, const FinalItem& f, uint64_t* sk, uint32
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kLocalThreads)
-k_local_sort(DevState* st, const FinalItem* items, uint64_t item_cap, Bufs B) {
-  constexpr int NT = kLocalThreads, IT = kLocalItems;
-  static_assert(NT * IT == kBucketCap, "one CTA holds one whole bucket");
+template <int NT, int IT>
+__device__ __forceinline__ void sort_bucket(const Bufs& B, const FinalItem& f,
+                                            const CtaSortSmem& s, uint64_t* red,
+                                            uint64_t* scan_sm) {
+  const uint32_t m = f.size;
+  uint64_t key[IT];
+  uint32_t idx[IT];
+#pragma unroll
+  for (int r = 0; r < IT; ++r) {
+    const uint32_t e = r * NT + threadIdx.x;
+    if (e < m) load_elem(B, f, e, key[r], idx[r]);
+  }
+  cta_sort_pairs<NT, IT>(key, idx, m, true, s, red, scan_sm);
+  for (uint32_t t = threadIdx.x; t < m; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
+  __syncthreads();
+}
+
+// Next item of size class cls for this CTA (atomic work counter), or -1.
+__device__ __forceinline__ int64_t next_item(DevState* st, int cls, uint64_t cap,
+                                             uint32_t* s_item) {
+  if (threadIdx.x == 0) *s_item = atomicAdd(&st->cursor_c[cls], 1u);
+  __syncthreads();
+  const uint32_t it = *s_item;
+  __syncthreads();
+  return it < umin64(st->nfinal_c[cls], cap) ? (int64_t)it : -1;
+}
+
+// Buckets of up to NT*IT keys, sorted by one CTA each (cta_sort_pairs).
+template <int NT, int IT, int CLS>
+__global__ void __launch_bounds__(NT, (NT == 128 ? 6 : 2))
+k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
+  constexpr int kCap = NT * IT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSortSmem s;
-  s.k = (uint64_t*)smem_raw;                // [kBucketCap]
-  s.i = (uint32_t*)(s.k + kBucketCap);      // [kBucketCap]
-  s.hist = s.i + kBucketCap;                // [kBucketCap]
+  s.k = (uint64_t*)smem_raw;          // [kCap]
+  s.i = (uint32_t*)(s.k + kCap);      // [kCap]
+  s.hist = s.i + kCap;                // [kCap]
   __shared__ uint64_t red[2 * NT / 32];
   __shared__ uint64_t scan_sm[NT / 32];
   __shared__ uint32_t s_item;
-  const uint64_t nitems = umin64(st->nfinal, item_cap);
+  const FinalItem* list = items + (uint64_t)CLS * cap;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&st->final_cursor, 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
-    __syncthreads();
-    if (it >= nitems) break;
-    const FinalItem f = items[it];
-    const uint32_t m = f.size;
-    if (f.kind == kKindCopy) {
-      if (f.where == kWhereOut && !B.f64) continue;  // already in place
-      for (uint32_t t = threadIdx.x; t < m; t += NT) {
-        uint64_t k; uint32_t i;
-        load_elem(B, f, t, k, i);
-        store_out(B, f.start + t, k, i);
-      }
-      continue;
-    }
-    if (f.kind == kKindBig) {
-      sort_big(B, f, s.k, s.i);
-      continue;
-    }
-    uint64_t key[IT];
-    uint32_t idx[IT];
-#pragma unroll
-    for (int r = 0; r < IT; ++r) {
-      const uint32_t e = r * NT + threadIdx.x;
-      if (e < m) load_elem(B, f, e, key[r], idx[r]);
-    }
-    cta_sort_pairs<NT, IT>(key, idx, m, true, s, red, scan_sm);
-    for (uint32_t t = threadIdx.x; t < m; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
-    __syncthreads();
+    const int64_t it = next_item(st, CLS, cap, &s_item);
+    if (it < 0) break;
+    sort_bucket<NT, IT>(B, list[it], s, red, scan_sm);
   }
 }
+
+// Copy-through buckets (size 1, or equality buckets already in position
+// order): a coalesced copy that restores float64 bit patterns.
+__global__ void __launch_bounds__(256)
+k_local_copy(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
+  __shared__ uint32_t s_item;
+  const FinalItem* list = items + (uint64_t)kClassCopy * cap;
+  for (;;) {
+    const int64_t it = next_item(st, kClassCopy, cap, &s_item);
+    if (it < 0) break;
+    const FinalItem f = list[it];
+    if (f.where == kWhereOut && !B.f64) continue;  // already in place
+    for (uint32_t t = threadIdx.x; t < f.size; t += blockDim.x) {
+      uint64_t k;
+      uint32_t i;
+      load_elem(B, f, t, k, i);
+      store_out(B, f.start + t, k, i);
+    }
+  }
+}
+
+// Oversize buckets (after the last partition level; vanishingly rare).
+__global__ void __launch_bounds__(kLocalThreads)
+k_local_big(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* sk = (uint64_t*)smem_raw;
+  uint32_t* si = (uint32_t*)(sk + kBucketCap);
+  __shared__ uint32_t s_item;
+  const FinalItem* list = items + (uint64_t)kClassBig * cap;
+  for (;;) {
+    const int64_t it = next_item(st, kClassBig, cap, &s_item);
+    if (it < 0) break;
+    sort_big(B, list[it], sk, si);
+  }
+}
+
+constexpr int kSmallThreads = 128;
+constexpr int kSmallItems = kSmallCap / kSmallThreads;  // 8
+static_assert(kSmallThreads * kSmallItems == (int)kSmallCap, "small class fits one CTA");
+static_assert(kLocalThreads * kLocalItems == kBucketCap, "medium class fits one CTA");
 
 }  // namespace
 
 void set_local_kernel_attributes() {
-  cudaFuncSetAttribute(k_local_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kBucketCap * (8 + 4 + 4));
+  cudaFuncSetAttribute(k_local_sort<kSmallThreads, kSmallItems, kClassSmall>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * 16);
+  cudaFuncSetAttribute(k_local_sort<kLocalThreads, kLocalItems, kClassMedium>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * 16);
+  cudaFuncSetAttribute(k_local_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kBucketCap * 12);
 }
 
 void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
@@ -196,9 +241,24 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   B.out = out;
   B.tmp = tmp;
   B.f64 = f64;
-  const int smem = kBucketCap * (8 + 4 + 4);
-  Scope sc(e, "local_sort");
-  k_local_sort<<<e.num_sms * 3, kLocalThreads, smem, e.stream>>>(st, items, item_cap, B);
+  {
+    Scope sc(e, "local_copy");
+    k_local_copy<<<e.num_sms * 4, 256, 0, e.stream>>>(st, items, item_cap, B);
+  }
+  {
+    Scope sc(e, "local_sort");
+    k_local_sort<kSmallThreads, kSmallItems, kClassSmall>
+        <<<e.num_sms * 6, kSmallThreads, kSmallCap * 16, e.stream>>>(st, items, item_cap, B);
+  }
+  {
+    Scope sc(e, "local_sort_medium");
+    k_local_sort<kLocalThreads, kLocalItems, kClassMedium>
+        <<<e.num_sms * 2, kLocalThreads, kBucketCap * 16, e.stream>>>(st, items, item_cap, B);
+  }
+  {
+    Scope sc(e, "local_big");
+    k_local_big<<<e.num_sms, kLocalThreads, kBucketCap * 12, e.stream>>>(st, items, item_cap, B);
+  }
 }
 
 }  // namespace rsort

@@ -115,6 +115,7 @@ extern "C" rsort_status rsort_partition_noalloc(rsort_key_type type, const void*
   P.schunk_cap = samp / kSampleChunk + 2;
   P.bucket_cap = kk;
   P.level1_oversample = 1;
+  P.classifier = 0;
 
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) {
@@ -142,7 +143,7 @@ extern "C" rsort_status rsort_partition_noalloc(rsort_key_type type, const void*
   e.launches = nullptr;
   // The control block is reset by the first kernel; every other scratch word
   // read later is written earlier in the same call.
-  launch_init_plain(e, st, list1, items, n, k, 0);
+  launch_init_plain(e, st, list1, items, n, k, 0, 1);
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
   launch_level(e, P, st, list1, list0, segs, src, dst, kWhereOut, samp_key, samp_idx, ssamp_key,

@@ -13,6 +13,7 @@
 // the paper's sample sort becomes the scan + scatter through HBM.
 #include <cstdio>
 
+#include "async_copy.cuh"
 #include "cta_sort.cuh"
 #include "rsort_internal.cuh"
 
@@ -59,18 +60,35 @@ __device__ __forceinline__ uint64_t load_key(const Src& s, uint64_t pos) {
 //
 // The k-1 splitters of a segment are the sorted sample's elements
 // floor(j*S/k), j = 1..k-1 (Appendix "Generalizing Quicksort": every S/k-th
-// sample), kept as (key, position) pairs.  Their keys are also laid out as an
-// implicit binary search tree (Eytzinger order, padded with UINT64_MAX to
-// Kp - 1 = next_pow2(k) - 1 nodes): the branchless classifier of Super Scalar
-// Sample Sort that the appendix names.
+// sample), kept as sorted (key, position) pairs.  Two classifiers search them,
+// both returning the same bucket:
+//   tree   the branchless implicit search tree of Super Scalar Sample Sort that
+//          the appendix names: the keys in Eytzinger order, padded with
+//          UINT64_MAX to Kp - 1 = next_pow2(k) - 1 nodes;
+//   table  a lookup table over the leading bits of (key - smallest splitter
+//          key) giving, for every bin, the range of splitters whose key falls
+//          in it; a key is located by one table read and a binary search over
+//          its bin's splitters (a full binary search when keys cluster).
 // ---------------------------------------------------------------------------
+constexpr int kTableBitsMax = 12;
+
 struct Splitters {
-  uint64_t* tree;   // [Kp]   node i at tree[i], i = 1..Kp-1
+  uint64_t* tree;   // [Kp]   node i at tree[i], i = 1..Kp-1          (tree mode)
+  uint32_t* tbl;    // [2^tbits] packed (first, end) splitter of a bin (table mode)
   uint64_t* key;    // [k-1]  sorted splitter keys
   uint32_t* idx;    // [k-1]  their positions (tie-breakers)
+  uint64_t lo, hi;  // smallest / largest splitter key
   int logK;         // log2(Kp)
+  int tbits;        // table bits
+  int shift;        // key bits dropped before the table index
+  int mode;         // 0 tree, 1 table
   uint32_t nspl;    // k - 1
 };
+
+__host__ __device__ inline int table_bits_for(uint32_t kp) {
+  const int b = log2_u32(kp) + 1;
+  return b < kTableBitsMax ? b : kTableBitsMax;
+}
 
 template <int NT>
 __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const uint32_t* ssi,
@@ -85,11 +103,37 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
     sp.idx[j] = ssi[sg.samp_off + r];
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x + 1; i < Kp; i += NT) {
-    const int d = 31 - __clz(i);
-    const uint32_t r = i - (1u << d);
-    const uint32_t in = ((2 * r + 1) << (sp.logK - 1 - d)) - 1;
-    sp.tree[i] = in < sp.nspl ? sp.key[in] : ~0ULL;
+  if (sp.mode == 0) {
+    for (uint32_t i = threadIdx.x + 1; i < Kp; i += NT) {
+      const int d = 31 - __clz(i);
+      const uint32_t r = i - (1u << d);
+      const uint32_t in = ((2 * r + 1) << (sp.logK - 1 - d)) - 1;
+      sp.tree[i] = in < sp.nspl ? sp.key[in] : ~0ULL;
+    }
+  } else if (sp.nspl > 0) {
+    sp.lo = sp.key[0];
+    sp.hi = sp.key[sp.nspl - 1];
+    const uint64_t range = sp.hi - sp.lo;
+    const int bits = range ? 64 - __clzll((long long)range) : 0;
+    sp.tbits = table_bits_for(Kp);
+    sp.shift = bits > sp.tbits ? bits - sp.tbits : 0;
+    const uint32_t T = 1u << sp.tbits;
+    // first splitter whose bin is >= t, by binary search over the sorted keys
+    auto first_at_least = [&](uint32_t t) {
+      uint32_t lo = 0, hi = sp.nspl;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (((sp.key[mid] - sp.lo) >> sp.shift) < t) lo = mid + 1; else hi = mid;
+      }
+      return lo;
+    };
+    for (uint32_t t = threadIdx.x; t < T; t += NT)
+      sp.tbl[t] = first_at_least(t) | (first_at_least(t + 1) << 16);
+  } else {
+    sp.lo = ~0ULL;
+    sp.hi = 0;
+    sp.tbits = 0;
+    sp.shift = 0;
   }
   __syncthreads();
 }
@@ -101,9 +145,19 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
 // node where it turned left, which is the bounding splitter's key; only if x
 // equals it is the search repeated on the run of equal splitter keys with
 // positions as tie-breakers (pos_of(r) is evaluated only then).
+__device__ __forceinline__ uint32_t tie_break(uint32_t bb, uint64_t x, uint32_t i,
+                                              const Splitters& sp) {
+  uint32_t lo = bb, hi = sp.nspl;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (sp.key[mid] == x && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 template <int R, typename PosFn>
-__device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t (&b)[R],
-                                               PosFn pos_of, const Splitters& sp) {
+__device__ __forceinline__ void classify_batch_tree(const uint64_t (&x)[R], uint32_t (&b)[R],
+                                                    PosFn pos_of, const Splitters& sp) {
   uint32_t j[R];
   uint64_t ub[R];
 #pragma unroll
@@ -123,17 +177,55 @@ __device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t 
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     uint32_t bb = j[r] - (1u << sp.logK);
-    if (bb < sp.nspl && ub[r] == x[r]) {
-      const uint32_t i = pos_of(r);
-      uint32_t lo = bb, hi = sp.nspl;
+    if (bb < sp.nspl && ub[r] == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
+    b[r] = bb;
+  }
+}
+
+// Same result through the leading-bits table: one table read per element, then
+// a lower-bound search over the splitters of its bin (usually 0-2 of them).
+template <int R, typename PosFn>
+__device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uint32_t (&b)[R],
+                                                     PosFn pos_of, const Splitters& sp) {
+  uint32_t pr[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const bool inside = x[r] >= sp.lo && x[r] <= sp.hi;
+    pr[r] = inside ? sp.tbl[(uint32_t)((x[r] - sp.lo) >> sp.shift)] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    uint32_t bb;
+    if (x[r] < sp.lo || sp.nspl == 0) {
+      bb = 0;
+    } else if (x[r] > sp.hi) {
+      bb = sp.nspl;
+    } else {
+      uint32_t lo = pr[r] & 0xffffu, hi = pr[r] >> 16;
+      const uint32_t end = hi;
+      uint64_t ub = ~0ULL;
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (sp.key[mid] == x[r] && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
+        const uint64_t km = sp.key[mid];
+        if (km < x[r]) {
+          lo = mid + 1;
+        } else {
+          hi = mid;
+          ub = km;
+        }
       }
       bb = lo;
+      if (bb < end && ub == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
     }
     b[r] = bb;
   }
+}
+
+template <int R, typename PosFn>
+__device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t (&b)[R],
+                                               PosFn pos_of, const Splitters& sp) {
+  if (sp.mode == 0) classify_batch_tree<R>(x, b, pos_of, sp);
+  else classify_batch_table<R>(x, b, pos_of, sp);
 }
 
 // ---------------------------------------------------------------------------
@@ -141,11 +233,13 @@ __device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t 
 // ---------------------------------------------------------------------------
 
 __global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uint64_t n,
-                             uint32_t k1, int direct) {
+                             uint32_t k1, int direct, uint64_t final_cap) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->nseg[0] = st->nseg[1] = 0;
-  st->nfinal = 0;
-  st->final_cursor = 0;
+  for (int c = 0; c < kNumClasses; ++c) {
+    st->nfinal_c[c] = 0;
+    st->cursor_c[c] = 0;
+  }
   st->error = 0;
   st->max_bucket_l1 = 0;
   st->levels_used = 0;
@@ -162,8 +256,7 @@ __global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uin
     f.size = (uint32_t)n;
     f.where = kWhereInput;
     f.kind = n == 1 ? kKindCopy : kKindSort;
-    items[0] = f;
-    st->nfinal = 1;
+    push_final(st, items, final_cap, f, kErrFinalCap);
   } else {
     SegIn s;
     s.start = 0;
@@ -371,61 +464,88 @@ k_sample_merge_rank(const DevState* st, const LevelSeg* segs, const uint64_t* sa
 }
 
 // Shared-memory carve-up of the classify / scatter kernels.
+constexpr int kCT = 2048;                       // keys per classify pipeline stage
+constexpr int kCStages = 3;                     // classify stages (2 in flight)
+constexpr int kCItems = kCT / kPartThreads;     // 8 keys per lane per stage
+constexpr int kST = 2048;                       // keys per scatter sub-tile
+constexpr int kSItems = kST / kPartThreads;     // 8 keys per lane per sub-tile
+static_assert(kSItems * 32 * kPartWarps == kST, "warp w owns kSItems*32 consecutive keys");
+
 struct PartSmem {
   Splitters sp;
   uint32_t* hist;      // [K]   classify: counts;  scatter: running offsets
   uint32_t* sbase;     // [K+1] scatter: sub-tile bucket starts
-  uint16_t* wcnt;      // [kPartWarps][K] scatter: per-warp counts / bases
-  uint64_t* stg_key;   // [kSubTile]
-  uint32_t* stg_idx;   // [kSubTile]
-  uint16_t* stg_b;     // [kSubTile]
+  uint16_t* wcnt;      // [kPartWarps][cnt_stride(K)] scatter: per-warp counts / bases
+  unsigned char* buf;  // classify: kCStages key stages; scatter: two sub-tile buffers
 };
 
 // Per-warp counter rows are padded to an even length so a warp can clear its
 // row with 32-bit stores without touching the next warp's row.
 __host__ __device__ inline uint32_t cnt_stride(uint32_t kmax) { return (kmax + 1) & ~1u; }
 
-__host__ __device__ inline size_t part_smem_bytes(uint32_t kmax, bool scatter) {
+// one scatter sub-tile buffer: keys, positions, bucket ids
+constexpr size_t kSBufBytes = (size_t)kST * (8 + 4 + 2);
+
+__host__ __device__ inline size_t part_common_bytes(uint32_t kmax, int mode) {
   const size_t Kp = next_pow2_u32(kmax);
-  size_t b = Kp * 8 + (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
+  size_t b = mode == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
+  b += (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t part_smem_bytes(uint32_t kmax, bool scatter, int mode) {
+  size_t b = part_common_bytes(kmax, mode);
   if (scatter) {
-    b += (size_t)(kmax + 1) * 4 + 4;  // sbase, padded to 8 bytes
+    b += (size_t)(kmax + 1) * 4 + 4;
     b += (size_t)kPartWarps * cnt_stride(kmax) * 2;
     b = (b + 15) & ~(size_t)15;
-    b += (size_t)kSubTile * (8 + 4 + 2);
+    b += 2 * kSBufBytes;
+  } else {
+    b += (size_t)kCStages * kCT * 8;
   }
   return b;
 }
 
-__device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatter) {
+__device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatter, int mode) {
   PartSmem s;
   const size_t Kp = next_pow2_u32(kmax);
   unsigned char* p = base;
-  s.sp.tree = (uint64_t*)p; p += Kp * 8;
+  s.sp.mode = mode;
+  s.sp.tree = nullptr;
+  s.sp.tbl = nullptr;
+  if (mode == 0) {
+    s.sp.tree = (uint64_t*)p;
+    p += Kp * 8;
+  } else {
+    s.sp.tbl = (uint32_t*)p;
+    p += (size_t)4 << table_bits_for((uint32_t)Kp);
+  }
   s.sp.key = (uint64_t*)p; p += (size_t)kmax * 8;
   s.sp.idx = (uint32_t*)p; p += (size_t)kmax * 4;
   s.hist = (uint32_t*)p; p += (size_t)kmax * 4;
-  s.sbase = nullptr; s.wcnt = nullptr; s.stg_key = nullptr; s.stg_idx = nullptr;
-  s.stg_b = nullptr;
+  p = base + part_common_bytes(kmax, mode);
+  s.sbase = nullptr;
+  s.wcnt = nullptr;
   if (scatter) {
     s.sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4 + 4;
     s.wcnt = (uint16_t*)p; p += (size_t)kPartWarps * cnt_stride(kmax) * 2;
     p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    s.stg_key = (uint64_t*)p; p += (size_t)kSubTile * 8;
-    s.stg_idx = (uint32_t*)p; p += (size_t)kSubTile * 4;
-    s.stg_b = (uint16_t*)p;
   }
+  s.buf = p;
   return s;
 }
 
 // Steps 4 + 5a: classify every element and count, per chunk of W elements,
 // how many fall into each bucket.  hist is laid out per segment bucket-major:
-// hist[hist_off + b * nchunks + chunk].
-__global__ void __launch_bounds__(kPartThreads)
+// hist[hist_off + b * nchunks + chunk].  The chunk's keys stream through a
+// kCStages-deep cp.async pipeline of kCT-key stages in shared memory.
+__global__ void __launch_bounds__(kPartThreads, 3)
 k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
-                 const uint32_t* ssi, uint32_t* hist, uint32_t W, uint32_t kmax) {
+                 const uint32_t* ssi, uint32_t* hist, uint32_t W, uint32_t kmax, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PartSmem sm = carve(smem_raw, kmax, false);
+  PartSmem sm = carve(smem_raw, kmax, false, mode);
+  uint64_t* stage = (uint64_t*)sm.buf;
+  const uint64_t pol = l2_evict_first_policy();
   const uint64_t total = st->total_chunks;
   const uint32_t G = st->cur_nseg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -439,36 +559,56 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
       cur_g = g;
     }
     for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads) sm.hist[b] = 0;
-    __syncthreads();
     const uint64_t cl = c - sg.chunk_off;
     const uint64_t cs = sg.start + cl * W;
     const uint64_t ce = umin64(cs + W, sg.start + sg.m);
-    for (uint64_t base = cs + (uint64_t)warp * kWarpSpan; base < ce;
-         base += (uint64_t)kPartWarps * kWarpSpan) {
-      uint64_t key[kItems];
-#pragma unroll
-      for (int r = 0; r < kItems; ++r) {
-        const uint64_t pos = base + r * 32 + lane;
-        key[r] = pos < ce ? load_key(src, pos) : 0;
+    const uint64_t nst = (ce - cs + kCT - 1) / kCT;
+    auto issue = [&](uint64_t s) {
+      if (s < nst) {
+        const uint64_t b0 = cs + s * kCT;
+        const uint32_t len = (uint32_t)umin64(kCT, ce - b0);
+        uint64_t* dst = stage + (s % kCStages) * kCT;
+        for (uint32_t t = threadIdx.x; t < len; t += kPartThreads)
+          cp_async_8(dst + t, src.key + b0 + t, pol);
       }
-      uint32_t bk[kItems];
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int s = 0; s < kCStages - 1; ++s) issue(s);
+    for (uint64_t s = 0; s < nst; ++s) {
+      cp_async_wait<kCStages - 2>();
+      __syncthreads();
+      issue(s + kCStages - 1);
+      const uint64_t b0 = cs + s * kCT;
+      const uint32_t len = (uint32_t)umin64(kCT, ce - b0);
+      const uint64_t* stg = stage + (s % kCStages) * kCT;
+      const uint32_t q0 = (uint32_t)warp * (kCItems * 32) + lane;
+      uint64_t key[kCItems];
+#pragma unroll
+      for (int r = 0; r < kCItems; ++r) {
+        const uint32_t q = q0 + r * 32;
+        const uint64_t k = q < len ? stg[q] : 0;
+        key[r] = src.map_f64 ? f64_to_ordered(k) : k;
+      }
+      uint32_t bk[kCItems];
       // positions are read only when a key ties with a splitter key
-      classify_batch<kItems>(key, bk, [&](int r) {
-        const uint64_t pos = base + r * 32 + lane;
-        return pos < ce ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0u;
+      classify_batch<kCItems>(key, bk, [&](int r) {
+        const uint64_t pos = b0 + q0 + r * 32;
+        return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
       }, sm.sp);
 #pragma unroll
-      for (int r = 0; r < kItems; ++r) {
-        const bool v = base + r * 32 + lane < ce;
+      for (int r = 0; r < kCItems; ++r) {
+        const bool v = q0 + r * 32 < len;
         const uint32_t b = bk[r];
-        const uint32_t b0 = __shfl_sync(0xffffffffu, b, 0);
-        if (__all_sync(0xffffffffu, v && b == b0)) {
-          if (lane == 0) atomicAdd(&sm.hist[b0], 32u);
+        const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
+        if (__all_sync(0xffffffffu, v && b == bl)) {
+          if (lane == 0) atomicAdd(&sm.hist[bl], 32u);
         } else if (v) {
           atomicAdd(&sm.hist[b], 1u);
         }
       }
     }
+    cp_async_wait<0>();
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads)
       hist[sg.hist_off + (uint64_t)b * sg.nchunks + cl] = sm.hist[b];
@@ -530,23 +670,43 @@ k_scan_down(const DevState* st, uint32_t* a, const uint32_t* sums) {
   }
 }
 
-// Step 5c: stable scatter.  Every chunk is processed in sub-tiles of kSubTile
-// elements; warp w owns 512 consecutive elements of the sub-tile.  Each
-// element's rank among the earlier elements of its bucket in the sub-tile is
-// computed with warp-synchronous match/ballot counting (warp order, then
-// lane order = input order), the sub-tile is counting-sorted by bucket in
-// shared memory, and runs of each bucket are written out contiguously
-// (write-combining through shared memory).  Buckets therefore keep input order.
-__global__ void __launch_bounds__(kPartThreads)
+// Step 5c: stable scatter.  Every chunk streams through two kST-key sub-tile
+// buffers (cp.async: sub-tile s+1 loads while s is processed).  Warp w owns
+// kSItems*32 consecutive elements of a sub-tile; an element's rank among the
+// earlier elements of its bucket in the sub-tile comes from warp-synchronous
+// match counting (warp order, then lane order = input order).  The sub-tile is
+// then counting-sorted by bucket into its own buffer and every bucket's run is
+// written out contiguously (write-combining through shared memory), so
+// buckets keep input order.
+__global__ void __launch_bounds__(kPartThreads, 2)
 k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
           const uint32_t* ssi, const uint32_t* hist_scan, Dst dst, uint32_t W, uint32_t kmax,
-          int unmap_out) {
+          int unmap_out, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PartSmem sm = carve(smem_raw, kmax, true);
+  PartSmem sm = carve(smem_raw, kmax, true, mode);
+  __shared__ uint64_t scan_sm[kPartWarps];
+  // sub-tile buffer i: keys, positions, bucket ids (addressed arithmetically so
+  // that no descriptor array lives in local memory)
+  struct Buf {
+    uint64_t* key;
+    uint32_t* idx;
+    uint16_t* b;
+  };
+  auto buf_of = [&](uint64_t i) {
+    unsigned char* p = sm.buf + (size_t)(i & 1) * kSBufBytes;
+    Buf r;
+    r.key = (uint64_t*)p;
+    r.idx = (uint32_t*)(p + (size_t)kST * 8);
+    r.b = (uint16_t*)(p + (size_t)kST * 12);
+    return r;
+  };
+  const uint64_t pol = l2_evict_first_policy();
   const uint64_t total = st->total_chunks;
   const uint32_t G = st->cur_nseg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t ltmask = lanemask_lt();
+  const uint32_t kst = cnt_stride(kmax);
+  uint16_t* my_cnt = sm.wcnt + (size_t)warp * kst;
   uint32_t cur_g = 0xffffffffu;
   for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
     const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
@@ -562,29 +722,46 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nchunks + cl] + sg.delta);
     const uint64_t cs = sg.start + cl * W;
     const uint64_t ce = umin64(cs + W, sg.start + sg.m);
-    const uint32_t kst = cnt_stride(kmax);
-    uint16_t* my_cnt = sm.wcnt + (size_t)warp * kst;
-    for (uint64_t sub = cs; sub < ce; sub += kSubTile) {
-      const uint32_t len = (uint32_t)umin64(kSubTile, ce - sub);
-      const uint64_t wbase = sub + (uint64_t)warp * kWarpSpan;
-      uint64_t key[kItems];
-      uint32_t idx[kItems];
-      uint32_t bk[kItems];
-      uint32_t lrank[kItems];
-#pragma unroll
-      for (int r = 0; r < kItems; ++r) {
-        const uint64_t pos = wbase + r * 32 + lane;
-        const bool v = pos < ce;
-        key[r] = v ? load_key(src, pos) : 0;
-        idx[r] = v ? (src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start)) : 0;
+    const uint64_t nst = (ce - cs + kST - 1) / kST;
+    auto issue = [&](uint64_t s) {
+      if (s < nst) {
+        const uint64_t b0 = cs + s * kST;
+        const uint32_t len = (uint32_t)umin64(kST, ce - b0);
+        const Buf B = buf_of(s);
+        for (uint32_t t = threadIdx.x; t < len; t += kPartThreads) {
+          cp_async_8(B.key + t, src.key + b0 + t, pol);
+          if (src.idx) cp_async_4(B.idx + t, src.idx + b0 + t, pol);
+        }
       }
+      cp_async_commit();
+    };
+    issue(0);
+    for (uint64_t s = 0; s < nst; ++s) {
+      cp_async_wait<0>();
+      __syncthreads();
+      issue(s + 1);
+      const Buf B = buf_of(s);
+      const uint64_t b0 = cs + s * kST;
+      const uint32_t len = (uint32_t)umin64(kST, ce - b0);
+      const uint32_t q0 = (uint32_t)warp * (kSItems * 32) + lane;
+      uint64_t key[kSItems];
+      uint32_t idx[kSItems];
+      uint32_t bk[kSItems];
+      uint32_t lrank[kSItems];
+#pragma unroll
+      for (int r = 0; r < kSItems; ++r) {
+        const uint32_t q = q0 + r * 32;
+        const bool v = q < len;
+        const uint64_t kv = v ? B.key[q] : 0;
+        key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
+        idx[r] = v ? (src.idx ? B.idx[q] : (uint32_t)(b0 + q - sg.start)) : 0;
+      }
+      classify_batch<kSItems>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
-      classify_batch<kItems>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
 #pragma unroll
-      for (int r = 0; r < kItems; ++r) {
-        const uint64_t pos = wbase + r * 32 + lane;
-        const bool v = pos < ce;
+      for (int r = 0; r < kSItems; ++r) {
+        const bool v = q0 + r * 32 < len;
         const uint32_t b = v ? bk[r] : 0xffffffffu;
         bk[r] = b;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
@@ -597,26 +774,25 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       __syncthreads();
       // per bucket: exclusive prefix over warps (in place) and the sub-tile total
       for (uint32_t b = threadIdx.x; b < k; b += kPartThreads) {
-        uint32_t s = 0;
+        uint32_t tot = 0;
 #pragma unroll
         for (int w = 0; w < kPartWarps; ++w) {
           const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
-          sm.wcnt[(size_t)w * kst + b] = (uint16_t)s;
-          s += cnt;
+          sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
+          tot += cnt;
         }
-        sm.sbase[b] = s;
+        sm.sbase[b] = tot;
       }
       __syncthreads();
-      // exclusive scan of the k sub-tile totals (one thread per run of buckets)
-      {
+      {  // exclusive scan of the k sub-tile totals (one thread per run of buckets)
         const uint32_t per = (k + kPartThreads - 1) / kPartThreads;
-        const uint32_t b0 = threadIdx.x * per;
+        const uint32_t bb0 = threadIdx.x * per;
+        const uint32_t bb1 = bb0 + per < k ? bb0 + per : k;
         uint32_t loc = 0;
-        for (uint32_t b = b0; b < min(k, b0 + per); ++b) loc += sm.sbase[b];
+        for (uint32_t b = bb0; b < bb1; ++b) loc += sm.sbase[b];
         uint64_t tot;
-        __shared__ uint64_t scan_sm[kPartWarps];
         uint32_t run = (uint32_t)block_excl_scan_u64<kPartThreads>(loc, &tot, scan_sm);
-        for (uint32_t b = b0; b < min(k, b0 + per); ++b) {
+        for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t t = sm.sbase[b];
           sm.sbase[b] = run;
           run += t;
@@ -624,29 +800,30 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         if (threadIdx.x == 0) sm.sbase[k] = len;
       }
       __syncthreads();
+      // counting-sort the sub-tile by bucket into its own buffer
 #pragma unroll
-      for (int r = 0; r < kItems; ++r) {
+      for (int r = 0; r < kSItems; ++r) {
         const uint32_t b = bk[r];
         if (b != 0xffffffffu) {
           const uint32_t q = sm.sbase[b] + my_cnt[b] + lrank[r];
-          sm.stg_key[q] = key[r];
-          sm.stg_idx[q] = idx[r];
-          sm.stg_b[q] = (uint16_t)b;
+          B.key[q] = key[r];
+          B.idx[q] = idx[r];
+          B.b[q] = (uint16_t)b;
         }
       }
       __syncthreads();
       for (uint32_t q = threadIdx.x; q < len; q += kPartThreads) {
-        const uint32_t b = sm.stg_b[q];
+        const uint32_t b = B.b[q];
         const uint64_t d = (uint64_t)sm.hist[b] + (q - sm.sbase[b]);
-        const uint64_t kv = sm.stg_key[q];
+        const uint64_t kv = B.key[q];
         dst.key[d] = unmap_out ? ordered_to_f64(kv) : kv;
-        dst.idx[d] = sm.stg_idx[q];
+        dst.idx[d] = B.idx[q];
       }
       __syncthreads();
       for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
         sm.hist[b] += sm.sbase[b + 1] - sm.sbase[b];
-      __syncthreads();
     }
+    cp_async_wait<0>();
   }
 }
 
@@ -691,9 +868,7 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
       it.where = where;
       it.kind = (eq || size == 1) ? kKindCopy : (size <= kBucketCap ? kKindSort : kKindBig);
       if (it.kind == kKindBig) atomicAdd((unsigned long long*)&st->big_items, 1ull);
-      const uint32_t slot = atomicAdd(&st->nfinal, 1u);
-      if (slot < P.final_cap) items[slot] = it;
-      else atomicOr(&st->error, kErrFinalCap);
+      push_final(st, items, P.final_cap, it, kErrFinalCap);
     } else {
       SegIn s;
       s.start = start;
@@ -715,20 +890,29 @@ inline int grid_for(uint64_t work, int per_block, int max_blocks) {
 }  // namespace
 
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
-                       uint64_t n, uint32_t k1, int direct) {
+                       uint64_t n, uint32_t k1, int direct, uint64_t final_cap) {
   Scope sc(e, "init");
-  k_init_plain<<<1, 32, 0, e.stream>>>(st, list0, items, n, k1, direct);
+  k_init_plain<<<1, 32, 0, e.stream>>>(st, list0, items, n, k1, direct, final_cap);
 }
-
-size_t part_smem_bytes_host(uint32_t kmax, bool scatter) { return part_smem_bytes(kmax, scatter); }
 
 void set_partition_kernel_attributes() {
   cudaFuncSetAttribute(k_sample_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kSampleChunk * (8 + 4 + 4));
-  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)part_smem_bytes(kMaxK, false));
-  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)part_smem_bytes(kMaxK, true));
+  const size_t c = umax64(part_smem_bytes(kMaxK, false, 0), part_smem_bytes(kMaxK, false, 1));
+  const size_t s = umax64(part_smem_bytes(kMaxK, true, 0), part_smem_bytes(kMaxK, true, 1));
+  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
+  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s);
+}
+
+// Resident CTAs per SM of the classify / scatter kernels for a bucket bound.
+int part_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
+  int nb = 0;
+  const size_t smem = part_smem_bytes(kmax, scatter, mode);
+  if (scatter)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter, kPartThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count, kPartThreads, smem);
+  return nb > 0 ? nb : 1;
 }
 
 // Segmented input: every segment [offsets[s], offsets[s+1]) is checked and
@@ -755,9 +939,7 @@ k_init_segments(DevState* st, const uint64_t* offsets, uint32_t nseg, uint64_t n
       f.size = (uint32_t)m;
       f.where = kWhereInput;
       f.kind = m == 1 ? kKindCopy : kKindSort;
-      const uint32_t slot = atomicAdd(&st->nfinal, 1u);
-      if (slot < final_cap) items[slot] = f;
-      else atomicOr(&st->error, kErrFinalCap);
+      push_final(st, items, final_cap, f, kErrFinalCap);
     } else {
       SegIn in;
       in.start = a;
@@ -818,13 +1000,17 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
     k_sample_merge_rank<<<grid_for(P.samp_cap, 256, sms * 8), 256, 0, e.stream>>>(
         st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
   }
-  const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false);
-  const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true);
-  const int part_grid = grid_for(P.chunk_cap, 1, sms * 2);
+  const int mode = P.classifier;
+  const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false, mode);
+  const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true, mode);
+  const int grid_c =
+      grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, false, mode));
+  const int grid_s =
+      grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode));
   {
     Scope sc(e, nm[4]);
-    k_classify_count<<<part_grid, kPartThreads, smem_c, e.stream>>>(
-        st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level);
+    k_classify_count<<<grid_c, kPartThreads, smem_c, e.stream>>>(
+        st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
   }
   const int scan_grid = (int)((P.hist_cap + kScanTile - 1) / kScanTile);
   {
@@ -841,8 +1027,9 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   {
     Scope sc(e, nm[8]);
-    k_scatter<<<part_grid, kPartThreads, smem_s, e.stream>>>(
-        st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out);
+    k_scatter<<<grid_s, kPartThreads, smem_s, e.stream>>>(
+        st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
+        mode);
   }
   {
     Scope sc(e, nm[9]);

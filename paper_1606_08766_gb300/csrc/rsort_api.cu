@@ -18,7 +18,6 @@
 #include "rsort_internal.cuh"
 
 namespace rsort {
-size_t part_smem_bytes_host(uint32_t kmax, bool scatter);
 
 // ---------------------------------------------------------------------------
 // Kernel timer: a pair of CUDA events around every launch, resolved lazily.
@@ -100,6 +99,7 @@ struct rsort_ctx {
   DevState* h_state = nullptr;  // pinned read-back buffer
   uint64_t launches = 0;
   bool profiling = false;
+  int classifier = 0;  // tunable "classifier": 0 splitter tree, 1 leading-bits table
   KernelTimer timer;
   TimerImpl timer_impl;
   std::mutex mu;
@@ -133,6 +133,7 @@ struct Plan {
   uint64_t bucket_cap = 0, final_cap = 0;
   uint64_t samp_cap1 = 0, hist_cap1 = 0, chunk_cap1 = 0, schunk_cap1 = 0, bucket_cap1 = 0;
   bool need_tmp = false;
+  int classifier = 0;       // 0: splitter tree, 1: leading-bits table
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
@@ -153,7 +154,7 @@ void layout(Plan& p) {
     return at;
   };
   p.off_state = take(sizeof(DevState));
-  p.off_items = take(p.final_cap * sizeof(FinalItem));
+  p.off_items = take((size_t)kNumClasses * p.final_cap * sizeof(FinalItem));
   if (p.need_tmp) {
     p.off_tmp_key = take(p.n * 8);
     p.off_tmp_idx = take(p.n * 4);
@@ -176,7 +177,9 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   p.n = n;
   p.k1 = k1;
   p.levels = levels;
-  const uint64_t per = (n + 2ull * num_sms - 1) / (2ull * num_sms);
+  // level 1 of one segment: 6 chunks per SM, so grids of 1, 2, 3 or 6 resident
+  // CTAs per SM all get the same number of chunks
+  const uint64_t per = (n + 6ull * num_sms - 1) / (6ull * num_sms);
   p.W1 = (uint32_t)std::max<uint64_t>(kSubTile, align_up(per, kSubTile));
   if (g1 > 1) p.W1 = 65536;
   p.Wd = 65536;
@@ -227,6 +230,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed) {
     P.bucket_cap = p.bucket_cap;
   }
   P.level1_oversample = 1;
+  P.classifier = p.classifier;
   return P;
 }
 
@@ -306,6 +310,15 @@ void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, D
                     type == RSORT_KEY_F64);
 }
 
+rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
+  if (strcmp(name, "classifier") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->classifier = (int)v;
+    return RSORT_OK;
+  }
+  return RSORT_EINVAL;
+}
+
 LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   LaunchEnv e;
   e.stream = s;
@@ -343,13 +356,28 @@ rsort_status rsort_create(rsort_ctx** out, int device, uint64_t hbm_budget_bytes
     cudaGetLastError();
     return RSORT_EINVAL;
   }
-  if (tune_table_path) {
-    FILE* f = fopen(tune_table_path, "r");
-    if (!f) return RSORT_EINVAL;
-    fclose(f);
-  }
   rsort_ctx* c = new (std::nothrow) rsort_ctx();
   if (!c) return RSORT_ENOMEM;
+  if (tune_table_path) {
+    // "name value" lines; '#' starts a comment
+    FILE* f = fopen(tune_table_path, "r");
+    if (!f) {
+      delete c;
+      return RSORT_EINVAL;
+    }
+    char line[256];
+    while (fgets(line, sizeof line, f)) {
+      char name[128];
+      long long v;
+      if (line[0] == '#') continue;
+      if (sscanf(line, "%127s %lld", name, &v) == 2 && set_tunable(c, name, v) != RSORT_OK) {
+        fclose(f);
+        delete c;
+        return RSORT_EINVAL;
+      }
+    }
+    fclose(f);
+  }
   c->device = device;
   c->budget = hbm_budget_bytes;
   DeviceGuard g(device);
@@ -424,6 +452,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
     return cuda_status(c);
   }
   Plan p;
+  p.classifier = c->classifier;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -433,7 +462,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   if (rs != RSORT_OK) return latch(c, rs);
   DevState* st = at<DevState>(c, p.off_state);
   SegIn* list1 = at<SegIn>(c, p.off_list1);
-  launch_init_plain(e, st, list1, at<FinalItem>(c, p.off_items), n, k, 0);
+  launch_init_plain(e, st, list1, at<FinalItem>(c, p.off_items), n, k, 0, p.final_cap);
   LevelParams P = level_params(p, 1, seed);
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
@@ -465,6 +494,7 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
   if (n == 0) return RSORT_OK;
   LaunchEnv e = env_of(c, s);
   Plan p;
+  p.classifier = c->classifier;
   const int direct = n <= (uint64_t)kBucketCap;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (direct) {
@@ -482,7 +512,7 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
   DevState* st = at<DevState>(c, p.off_state);
   FinalItem* items = at<FinalItem>(c, p.off_items);
   SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
-  launch_init_plain(e, st, lists[1], items, n, k1, direct);
+  launch_init_plain(e, st, lists[1], items, n, k1, direct, p.final_cap);
   Dst out{(uint64_t*)d_keys_out, d_perm_out};
   Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
   if (direct) p.levels = 0;
@@ -502,7 +532,8 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
     opt_stats->max_bucket = direct ? (uint32_t)n : h.max_bucket_l1;
     const double mean = opt_stats->p ? (double)n / opt_stats->p : (double)n;
     opt_stats->max_over_mean = mean > 0 ? opt_stats->max_bucket / mean : 0.0;
-    opt_stats->final_buckets = h.nfinal;
+    opt_stats->final_buckets = 0;
+    for (int i = 0; i < kNumClasses; ++i) opt_stats->final_buckets += h.nfinal_c[i];
     // level 1 reads 8 B/key twice and writes 12; deeper levels read 8 + 12 and
     // write 12; the in-SM sort reads and writes 12 B/key.
     uint64_t bytes = 24ull * n;
@@ -536,6 +567,7 @@ rsort_status rsort_segmented(rsort_ctx* c, rsort_key_type type, const void* d_ke
   if (n == 0 || num_segments == 0) return RSORT_OK;
   LaunchEnv e = env_of(c, s);
   Plan p;
+  p.classifier = c->classifier;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
   p.final_cap += num_segments;
@@ -546,7 +578,7 @@ rsort_status rsort_segmented(rsort_ctx* c, rsort_key_type type, const void* d_ke
   DevState* st = at<DevState>(c, p.off_state);
   FinalItem* items = at<FinalItem>(c, p.off_items);
   SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
-  launch_init_plain(e, st, lists[1], items, 0, 0, 0);  // reset the control block
+  launch_init_plain(e, st, lists[1], items, 0, 0, 0, p.final_cap);  // reset the control block
   launch_init_segments(e, st, d_offsets, num_segments, n, lists[1], items, p.seg_cap,
                        p.final_cap);
   Dst out{(uint64_t*)d_keys_out, d_perm_out};
@@ -587,6 +619,22 @@ rsort_status rsort_phase_times(rsort_ctx* c, const char** names, double* ms, uin
   c->timer_impl.acc.clear();
   c->timer_impl.order.clear();
   return cuda_status(c);
+}
+
+rsort_status rsort_set_tunable(rsort_ctx* c, const char* name, int64_t value) {
+  if (!c || !name) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return set_tunable(c, name, value);
+}
+
+rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
+  if (!c || !name || !value) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (strcmp(name, "classifier") == 0) {
+    *value = c->classifier;
+    return RSORT_OK;
+  }
+  return RSORT_EINVAL;
 }
 
 rsort_status rsort_launch_count(rsort_ctx* c, uint64_t* out) {

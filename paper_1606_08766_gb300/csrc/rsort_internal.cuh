@@ -33,6 +33,10 @@ constexpr int kScanTile = 4096;                   // device scan tile (1024 x 4)
 enum : uint16_t { kWhereOut = 0, kWhereTmp = 1, kWhereInput = 2 };
 // How a final bucket is finished.
 enum : uint16_t { kKindSort = 0, kKindCopy = 1, kKindBig = 2 };
+// Work lists of the in-SM sort, one per size class (each has its own kernel):
+// copy-through, <= kSmallCap keys, <= kBucketCap keys, oversize.
+enum : int { kClassCopy = 0, kClassSmall = 1, kClassMedium = 2, kClassBig = 3, kNumClasses = 4 };
+constexpr uint32_t kSmallCap = 1024;
 
 // A segment waiting to be partitioned (input of a level).
 struct SegIn {
@@ -71,8 +75,8 @@ struct FinalItem {
 // Device-resident control block of one call.
 struct DevState {
   uint32_t nseg[2];         // segment lists (ping-pong by level parity)
-  uint32_t nfinal;          // final items
-  uint32_t final_cursor;    // work counter of the in-SM sort
+  uint32_t nfinal_c[4];     // final items per size class
+  uint32_t cursor_c[4];     // work counters of the in-SM sort kernels
   uint32_t error;           // capacity / wait errors (bit flags)
   uint32_t max_bucket_l1;   // largest level-1 bucket
   uint32_t levels_used;
@@ -104,6 +108,7 @@ struct LevelParams {
   uint64_t seed;
   uint64_t samp_cap, hist_cap, chunk_cap, seg_cap, final_cap, schunk_cap, bucket_cap;
   int level1_oversample;  // 1: a = 16 ceil(log2 k) for hinted k (the paper's rule)
+  int classifier;         // 0: splitter tree, 1: leading-bits table
 };
 
 // Element source / destination of a level.
@@ -203,6 +208,18 @@ __device__ __forceinline__ void block_bitonic_sort(uint64_t* sk, uint32_t* si, i
 }
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// Appends a final bucket to the work list of its size class
+// (items holds kNumClasses lists of cap entries each).
+__device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint64_t cap,
+                                           const FinalItem& f, uint32_t err_flag) {
+  const int cls = f.kind == kKindCopy ? kClassCopy
+                  : f.kind == kKindBig ? kClassBig
+                  : (f.size <= kSmallCap ? kClassSmall : kClassMedium);
+  const uint32_t slot = atomicAdd(&st->nfinal_c[cls], 1u);
+  if (slot < cap) items[(uint64_t)cls * cap + slot] = f;
+  else atomicOr(&st->error, err_flag);
+}
 __host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
 __host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
@@ -234,7 +251,7 @@ struct LaunchEnv {
 };
 
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
-                       uint64_t n, uint32_t k1, int direct);
+                       uint64_t n, uint32_t k1, int direct, uint64_t final_cap);
 void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const SegIn* list_in,
                   SegIn* list_out, LevelSeg* segs, Src src, Dst dst, uint16_t dst_where,
                   uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,

@@ -188,3 +188,42 @@ def test_full_size_2p28(ctx, name):
         assert st.max_over_mean < 1.35
     del t, ko, po
     torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def ctx_table():
+    from paper_1606_08766_gb300 import Context
+    c = Context(0)
+    c.set_tunable("classifier", 1)
+    assert c.get_tunable("classifier") == 1
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("name,k", PART_CASES)
+def test_partition_table_classifier_matches_oracle(ctx_table, oracle_mod, name, k):
+    n = (1 << 17) + 1237
+    keys = instances.generate(name, n, p=64, seed=7)
+    ref = oracle_mod.partition(keys, k, seed=5)
+    ko, po, off = ctx_table.partition(_dev(keys), k, seed=5)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+    np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
+    np.testing.assert_array_equal(_host_u64(ko), ref["keys_out"])
+
+
+@pytest.mark.parametrize("name", instances.NAMES)
+def test_sort_table_classifier_matches_oracle(ctx_table, oracle_mod, name):
+    n = (1 << 20) + 77
+    keys = instances.generate(name, n, p=64, seed=1)
+    rk, rp = oracle_mod.sort(keys)
+    ko, po = ctx_table.sort(_dev(keys), p=64, seed=1)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+
+
+def test_tunable_rejects_unknown(ctx):
+    from paper_1606_08766_gb300 import RsortError
+    with pytest.raises(RsortError):
+        ctx.set_tunable("no_such_knob", 1)
+    with pytest.raises(RsortError):
+        ctx.set_tunable("classifier", 7)

@@ -6,7 +6,8 @@ must all come from their own allocator, real-time loops that forbid allocation
 after start-up.  This entry point takes its scratch from a fixed static device
 array inside librsort.  The test calls it through the C ABI twice in a row, on
 different inputs, and checks each result bit for bit against rsort_partition
-(the allocating entry point).  This file sorts last so a stop-at-first-failure
+(the allocating entry point), and that the call makes no allocation through
+torch's allocator.  This file sorts last so a stop-at-first-failure
 run has already run every other test.
 """
 import numpy as np
@@ -30,10 +31,12 @@ def test_noalloc_matches_partition_on_two_calls_in_a_row():
             po = torch.empty(n, dtype=torch.int32, device="cuda")
             oo = torch.empty(k + 1, dtype=torch.int64, device="cuda")
             torch.cuda.synchronize()
-            before = torch.cuda.memory_allocated()
+            # torch's count of allocations ever made (frees by garbage
+            # collection do not change it)
+            before = torch.cuda.memory_stats()["allocation.all.allocated"]
             partition_noalloc(keys, k, seed, ko, po, oo)
             torch.cuda.synchronize()
-            assert torch.cuda.memory_allocated() == before
+            assert torch.cuda.memory_stats()["allocation.all.allocated"] == before
             assert torch.equal(oo, ref_o)
             assert torch.equal(po, ref_p)
             assert torch.equal(ko, ref_k)
