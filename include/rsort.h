@@ -170,9 +170,14 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
 /* Tunables of a context (also settable from the tune table file given to
  * rsort_create, one "name value" per line).  They change speed, never
  * results.
- *   classifier   0: the splitter tree of Super Scalar Sample Sort (default);
- *                1: a lookup table over the keys' leading bits into the same
- *                sorted splitters, then a binary search inside the bin.
+ *   classifier   0: the splitter tree of Super Scalar Sample Sort;
+ *                1 (default): a lookup table over the keys' leading bits
+ *                into the same sorted splitters, then a binary search inside
+ *                the bin.
+ *   warp_direct_max_k  partition levels with at most this many buckets per
+ *                segment classify and scatter per warp sub-chunk straight to
+ *                HBM; larger levels stage every sub-tile through shared
+ *                memory (default 0: always staged).
  * Errors: EINVAL for an unknown name or an out-of-range value. */
 rsort_status rsort_set_tunable(rsort_ctx *ctx, const char *name, int64_t value);
 rsort_status rsort_get_tunable(rsort_ctx *ctx, const char *name, int64_t *value);

@@ -116,6 +116,7 @@ extern "C" rsort_status rsort_partition_noalloc(rsort_key_type type, const void*
   P.bucket_cap = kk;
   P.level1_oversample = 1;
   P.classifier = 0;
+  P.warp_direct = 0;
 
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) {

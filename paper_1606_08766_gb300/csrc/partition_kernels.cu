@@ -308,7 +308,7 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       nsch = (S + kSampleChunk - 1) / kSampleChunk;
       v[0] = S;
       v[1] = nch;
-      v[2] = (uint64_t)k * nch;
+      v[2] = (uint64_t)k * nch * (P.warp_direct ? kPartWarps : 1);
       v[3] = nsch;
       v[4] = k;
       v[5] = in.m;
@@ -331,7 +331,7 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       s.S = S;
       s.nchunks = nch;
       s.nschunks = nsch;
-      s.pad = 0;
+      s.nunits = nch * (P.warp_direct ? kPartWarps : 1);
       segs[g] = s;
     }
     __syncthreads();
@@ -611,7 +611,7 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
     cp_async_wait<0>();
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads)
-      hist[sg.hist_off + (uint64_t)b * sg.nchunks + cl] = sm.hist[b];
+      hist[sg.hist_off + (uint64_t)b * sg.nunits + cl] = sm.hist[b];
   }
 }
 
@@ -719,7 +719,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
     const uint32_t k = sg.k;
     const uint64_t cl = c - sg.chunk_off;
     for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
-      sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nchunks + cl] + sg.delta);
+      sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] + sg.delta);
     const uint64_t cs = sg.start + cl * W;
     const uint64_t ce = umin64(cs + W, sg.start + sg.m);
     const uint64_t nst = (ce - cs + kST - 1) / kST;
@@ -827,6 +827,218 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-direct variant of steps 4-5a / 5c.  Every chunk is split into
+// kPartWarps contiguous warp sub-chunks; the histogram has one unit per
+// (chunk, warp).  A warp streams its own sub-chunk through kWdStages
+// cp.async stages of kWdKeys keys (warp-level waits only), ranks elements
+// among equal buckets with match counting, and writes them straight to HBM
+// from warp-private running offsets.  No block barrier inside a chunk; the
+// order inside a bucket is still the input order.
+// ---------------------------------------------------------------------------
+constexpr int kWdItems = 4;                   // keys per lane per stage
+constexpr int kWdKeys = 32 * kWdItems;        // keys per warp per stage
+constexpr int kWdStages = 2;
+
+__host__ __device__ inline size_t wd_smem_bytes(uint32_t kmax, int mode) {
+  return part_common_bytes(kmax, mode) + (size_t)kPartWarps * kmax * 4 +
+         (size_t)kPartWarps * kWdStages * kWdKeys * (8 + 4);
+}
+
+struct WdSmem {
+  Splitters sp;
+  uint32_t* rows;   // [kPartWarps][kmax]: counts (classify) / next position (scatter)
+  uint64_t* skey;   // [kPartWarps][kWdStages][kWdKeys]
+  uint32_t* sidx;   // [kPartWarps][kWdStages][kWdKeys]
+};
+
+__device__ inline WdSmem carve_wd(unsigned char* base, uint32_t kmax, int mode) {
+  PartSmem ps = carve(base, kmax, false, mode);
+  WdSmem w;
+  w.sp = ps.sp;
+  unsigned char* p = base + part_common_bytes(kmax, mode);
+  w.rows = (uint32_t*)p;
+  p += (size_t)kPartWarps * kmax * 4;
+  w.skey = (uint64_t*)p;
+  p += (size_t)kPartWarps * kWdStages * kWdKeys * 8;
+  w.sidx = (uint32_t*)p;
+  return w;
+}
+
+// This warp's sub-chunk [ws, we) of chunk [cs, ce).
+__device__ __forceinline__ void warp_subchunk(uint64_t cs, uint64_t ce, int warp, uint64_t& ws,
+                                              uint64_t& we) {
+  const uint64_t cnt = ce - cs;
+  const uint64_t wsz = (cnt + kPartWarps - 1) / kPartWarps;
+  ws = cs + umin64((uint64_t)warp * wsz, cnt);
+  we = cs + umin64((uint64_t)(warp + 1) * wsz, cnt);
+}
+
+__global__ void __launch_bounds__(kPartThreads, 3)
+k_classify_count_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+                    const uint32_t* ssi, uint32_t* hist, uint32_t W, uint32_t kmax, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WdSmem sm = carve_wd(smem_raw, kmax, mode);
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* row = sm.rows + (size_t)warp * kmax;
+  uint64_t* stk = sm.skey + (size_t)warp * kWdStages * kWdKeys;
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    __syncthreads();
+    if (g != cur_g) {
+      load_splitters<kPartThreads>(sg, ssk, ssi, sm.sp);
+      cur_g = g;
+    }
+    const uint32_t k = sg.k;
+    for (uint32_t b = lane; b < k; b += 32) row[b] = 0;
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * W;
+    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    uint64_t ws, we;
+    warp_subchunk(cs, ce, warp, ws, we);
+    const uint64_t nsteps = (we - ws + kWdKeys - 1) / kWdKeys;
+    auto issue = [&](uint64_t t) {
+      if (t < nsteps) {
+        const uint64_t b0 = ws + t * kWdKeys;
+        uint64_t* dstk = stk + (t % kWdStages) * kWdKeys;
+#pragma unroll
+        for (int r = 0; r < kWdItems; ++r) {
+          const uint32_t q = r * 32 + lane;
+          if (b0 + q < we) cp_async_8(dstk + q, src.key + b0 + q, pol);
+        }
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    __syncwarp();
+    for (uint64_t t = 0; t < nsteps; ++t) {
+      issue(t + 1);
+      cp_async_wait<1>();
+      __syncwarp();
+      const uint64_t b0 = ws + t * kWdKeys;
+      const uint64_t* sk = stk + (t % kWdStages) * kWdKeys;
+      uint64_t key[kWdItems];
+#pragma unroll
+      for (int r = 0; r < kWdItems; ++r) {
+        const uint32_t q = r * 32 + lane;
+        const uint64_t kv = b0 + q < we ? sk[q] : 0;
+        key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
+      }
+      uint32_t bk[kWdItems];
+      classify_batch<kWdItems>(key, bk, [&](int r) {
+        const uint64_t pos = b0 + r * 32 + lane;
+        return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
+      }, sm.sp);
+#pragma unroll
+      for (int r = 0; r < kWdItems; ++r) {
+        const bool v = b0 + r * 32 + lane < we;
+        const uint32_t b = v ? bk[r] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (v && lane == __ffs(peers) - 1) row[b] += __popc(peers);
+        __syncwarp();
+      }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    for (uint32_t b = lane; b < k; b += 32)
+      hist[sg.hist_off + (uint64_t)b * sg.nunits + cl * kPartWarps + warp] = row[b];
+  }
+}
+
+__global__ void __launch_bounds__(kPartThreads, 3)
+k_scatter_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+             const uint32_t* ssi, const uint32_t* hist_scan, Dst dst, uint32_t W, uint32_t kmax,
+             int unmap_out, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WdSmem sm = carve_wd(smem_raw, kmax, mode);
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t ltmask = lanemask_lt();
+  uint32_t* row = sm.rows + (size_t)warp * kmax;
+  uint64_t* stk = sm.skey + (size_t)warp * kWdStages * kWdKeys;
+  uint32_t* sti = sm.sidx + (size_t)warp * kWdStages * kWdKeys;
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    __syncthreads();
+    if (g != cur_g) {
+      load_splitters<kPartThreads>(sg, ssk, ssi, sm.sp);
+      cur_g = g;
+    }
+    const uint32_t k = sg.k;
+    const uint64_t cl = c - sg.chunk_off;
+    for (uint32_t b = lane; b < k; b += 32)
+      row[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl * kPartWarps +
+                                    warp] + sg.delta);
+    const uint64_t cs = sg.start + cl * W;
+    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    uint64_t ws, we;
+    warp_subchunk(cs, ce, warp, ws, we);
+    const uint64_t nsteps = (we - ws + kWdKeys - 1) / kWdKeys;
+    auto issue = [&](uint64_t t) {
+      if (t < nsteps) {
+        const uint64_t b0 = ws + t * kWdKeys;
+        const size_t so = (t % kWdStages) * kWdKeys;
+#pragma unroll
+        for (int r = 0; r < kWdItems; ++r) {
+          const uint32_t q = r * 32 + lane;
+          if (b0 + q < we) {
+            cp_async_8(stk + so + q, src.key + b0 + q, pol);
+            if (src.idx) cp_async_4(sti + so + q, src.idx + b0 + q, pol);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+    issue(0);
+    __syncwarp();
+    for (uint64_t t = 0; t < nsteps; ++t) {
+      issue(t + 1);
+      cp_async_wait<1>();
+      __syncwarp();
+      const uint64_t b0 = ws + t * kWdKeys;
+      const size_t so = (t % kWdStages) * kWdKeys;
+      uint64_t key[kWdItems];
+      uint32_t idx[kWdItems];
+#pragma unroll
+      for (int r = 0; r < kWdItems; ++r) {
+        const uint32_t q = r * 32 + lane;
+        const bool v = b0 + q < we;
+        const uint64_t kv = v ? stk[so + q] : 0;
+        key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
+        idx[r] = v ? (src.idx ? sti[so + q] : (uint32_t)(b0 + q - sg.start)) : 0;
+      }
+      uint32_t bk[kWdItems];
+      classify_batch<kWdItems>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
+#pragma unroll
+      for (int r = 0; r < kWdItems; ++r) {
+        const bool v = b0 + r * 32 + lane < we;
+        const uint32_t b = v ? bk[r] : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const uint32_t c0 = v ? row[b] : 0;
+        __syncwarp();
+        if (v && lane == __ffs(peers) - 1) row[b] = c0 + __popc(peers);
+        __syncwarp();
+        if (v) {
+          const uint64_t d = (uint64_t)c0 + __popc(peers & ltmask);
+          dst.key[d] = unmap_out ? ordered_to_f64(key[r]) : key[r];
+          dst.idx[d] = idx[r];
+        }
+      }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+}
+
 // Collect the buckets of the level: bucket sizes follow from the scanned
 // histogram.  Buckets that fit one SM, equality buckets (both bounding
 // splitters share one key, so every element has that key and the stable
@@ -843,9 +1055,9 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
     const uint32_t g = find_seg(segs, G, f, [](const LevelSeg& x) { return x.bkt_off; });
     const LevelSeg& sg = segs[g];
     const uint32_t b = (uint32_t)(f - sg.bkt_off);
-    const uint64_t start = hist_scan[sg.hist_off + (uint64_t)b * sg.nchunks] + sg.delta;
+    const uint64_t start = hist_scan[sg.hist_off + (uint64_t)b * sg.nunits] + sg.delta;
     const uint64_t end = (b + 1 < sg.k)
-                             ? hist_scan[sg.hist_off + (uint64_t)(b + 1) * sg.nchunks] + sg.delta
+                             ? hist_scan[sg.hist_off + (uint64_t)(b + 1) * sg.nunits] + sg.delta
                              : sg.start + sg.m;
     const uint32_t size = (uint32_t)(end - start);
     if (offsets_out) {
@@ -902,6 +1114,19 @@ void set_partition_kernel_attributes() {
   const size_t s = umax64(part_smem_bytes(kMaxK, true, 0), part_smem_bytes(kMaxK, true, 1));
   cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
   cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s);
+  const size_t w = umax64(wd_smem_bytes(kMaxK, 0), wd_smem_bytes(kMaxK, 1));
+  cudaFuncSetAttribute(k_classify_count_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w);
+  cudaFuncSetAttribute(k_scatter_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w);
+}
+
+int wd_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
+  int nb = 0;
+  const size_t smem = wd_smem_bytes(kmax, mode);
+  if (scatter)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter_wd, kPartThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count_wd, kPartThreads, smem);
+  return nb > 0 ? nb : 1;
 }
 
 // Resident CTAs per SM of the classify / scatter kernels for a bucket bound.
@@ -1007,10 +1232,19 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, false, mode));
   const int grid_s =
       grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode));
+  const size_t smem_wd = wd_smem_bytes((uint32_t)kmax_level, mode);
+  const int grid_wd_c =
+      grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, false, mode));
+  const int grid_wd_s =
+      grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, true, mode));
   {
     Scope sc(e, nm[4]);
-    k_classify_count<<<grid_c, kPartThreads, smem_c, e.stream>>>(
-        st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
+    if (P.warp_direct)
+      k_classify_count_wd<<<grid_wd_c, kPartThreads, smem_wd, e.stream>>>(
+          st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
+    else
+      k_classify_count<<<grid_c, kPartThreads, smem_c, e.stream>>>(
+          st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
   }
   const int scan_grid = (int)((P.hist_cap + kScanTile - 1) / kScanTile);
   {
@@ -1027,9 +1261,14 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   {
     Scope sc(e, nm[8]);
-    k_scatter<<<grid_s, kPartThreads, smem_s, e.stream>>>(
-        st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
-        mode);
+    if (P.warp_direct)
+      k_scatter_wd<<<grid_wd_s, kPartThreads, smem_wd, e.stream>>>(
+          st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
+          mode);
+    else
+      k_scatter<<<grid_s, kPartThreads, smem_s, e.stream>>>(
+          st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
+          mode);
   }
   {
     Scope sc(e, nm[9]);

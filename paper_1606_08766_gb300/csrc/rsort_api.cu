@@ -99,7 +99,12 @@ struct rsort_ctx {
   DevState* h_state = nullptr;  // pinned read-back buffer
   uint64_t launches = 0;
   bool profiling = false;
-  int classifier = 0;  // tunable "classifier": 0 splitter tree, 1 leading-bits table
+  // tunable "classifier": 0 splitter tree, 1 leading-bits table (default: the
+  // table; both give the same buckets and the table measured faster on GB300)
+  int classifier = 1;
+  // tunable "warp_direct_max_k": warp-direct kernels up to this k (default off:
+  // direct scattered stores measured ~3x slower than shared-memory combining)
+  int wd_max_k = 0;
   KernelTimer timer;
   TimerImpl timer_impl;
   std::mutex mu;
@@ -134,6 +139,7 @@ struct Plan {
   uint64_t samp_cap1 = 0, hist_cap1 = 0, chunk_cap1 = 0, schunk_cap1 = 0, bucket_cap1 = 0;
   bool need_tmp = false;
   int classifier = 0;       // 0: splitter tree, 1: leading-bits table
+  int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
@@ -192,13 +198,14 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   const uint64_t a1 = k1 >= 2 ? 16ull * ceil_log2_host(k1) : (uint64_t)kDeepOversample;
   p.samp_cap1 = std::min<uint64_t>(n, a1 * p.bucket_cap1);
   p.chunk_cap1 = n / p.W1 + g1 + 1;
-  p.hist_cap1 = (uint64_t)kmax1 * (n / p.W1) + p.bucket_cap1;
+  // (x kPartWarps: a warp-direct level has one histogram unit per warp sub-chunk)
+  p.hist_cap1 = ((uint64_t)kmax1 * (n / p.W1) + p.bucket_cap1) * kPartWarps;
   p.schunk_cap1 = p.samp_cap1 / kSampleChunk + g1 + 1;
   // deeper levels
   const uint64_t bucket_capd = n / kTargetBucket + segs_deep + 1;
   const uint64_t samp_capd = std::min<uint64_t>(n, (uint64_t)kDeepOversample * bucket_capd);
   const uint64_t chunk_capd = n / p.Wd + segs_deep + 1;
-  const uint64_t hist_capd = (uint64_t)kMaxKDeep * (n / p.Wd) + bucket_capd;
+  const uint64_t hist_capd = ((uint64_t)kMaxKDeep * (n / p.Wd) + bucket_capd) * kPartWarps;
   const uint64_t schunk_capd = samp_capd / kSampleChunk + segs_deep + 1;
   const bool deep = levels > 1;
   p.bucket_cap = std::max<uint64_t>(p.bucket_cap1, deep ? bucket_capd : 0);
@@ -209,7 +216,7 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   p.final_cap = p.bucket_cap1 + (uint64_t)(levels - 1) * bucket_capd + 4;
 }
 
-LevelParams level_params(const Plan& p, int level, uint64_t seed) {
+LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level) {
   LevelParams P;
   P.level = level;
   P.W = level == 1 ? p.W1 : p.Wd;
@@ -231,6 +238,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed) {
   }
   P.level1_oversample = 1;
   P.classifier = p.classifier;
+  P.warp_direct = kmax_level <= p.wd_max_k ? 1 : 0;
   return P;
 }
 
@@ -289,7 +297,8 @@ void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, D
                               const void* d_keys_in, const Dst& out, const Dst& tmp,
                               uint64_t seed, uint32_t k1) {
   for (int L = 1; L <= p.levels; ++L) {
-    LevelParams P = level_params(p, L, seed);
+    const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
+    LevelParams P = level_params(p, L, seed, kmax);
     Src src;
     if (L == 1) {
       src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
@@ -299,7 +308,6 @@ void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, D
     }
     const Dst& dst = (L & 1) ? tmp : out;
     const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
-    const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
     launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(c, p.off_segs), src,
                  dst, where, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
                  at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
@@ -314,6 +322,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   if (strcmp(name, "classifier") == 0) {
     if (v != 0 && v != 1) return RSORT_EINVAL;
     c->classifier = (int)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "warp_direct_max_k") == 0) {
+    if (v < 0 || v > kMaxK) return RSORT_EINVAL;
+    c->wd_max_k = (int)v;
     return RSORT_OK;
   }
   return RSORT_EINVAL;
@@ -453,6 +466,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   }
   Plan p;
   p.classifier = c->classifier;
+  p.wd_max_k = c->wd_max_k;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -463,7 +477,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   DevState* st = at<DevState>(c, p.off_state);
   SegIn* list1 = at<SegIn>(c, p.off_list1);
   launch_init_plain(e, st, list1, at<FinalItem>(c, p.off_items), n, k, 0, p.final_cap);
-  LevelParams P = level_params(p, 1, seed);
+  LevelParams P = level_params(p, 1, seed, (int)kk);
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
   launch_level(e, P, st, list1, at<SegIn>(c, p.off_list0), at<LevelSeg>(c, p.off_segs), src, dst,
@@ -495,6 +509,7 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
   LaunchEnv e = env_of(c, s);
   Plan p;
   p.classifier = c->classifier;
+  p.wd_max_k = c->wd_max_k;
   const int direct = n <= (uint64_t)kBucketCap;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (direct) {
@@ -568,6 +583,7 @@ rsort_status rsort_segmented(rsort_ctx* c, rsort_key_type type, const void* d_ke
   LaunchEnv e = env_of(c, s);
   Plan p;
   p.classifier = c->classifier;
+  p.wd_max_k = c->wd_max_k;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
   p.final_cap += num_segments;
@@ -632,6 +648,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   std::lock_guard<std::mutex> lk(c->mu);
   if (strcmp(name, "classifier") == 0) {
     *value = c->classifier;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "warp_direct_max_k") == 0) {
+    *value = c->wd_max_k;
     return RSORT_OK;
   }
   return RSORT_EINVAL;

@@ -20,7 +20,8 @@ constexpr int kSubTile = kPartThreads * kItems;   // 4096 keys staged per sub-ti
 constexpr int kMaxK = 2048;                       // buckets per partition step
 constexpr int kMaxKDeep = 512;                    // buckets at levels >= 2
 constexpr int kBucketCap = 4096;                  // T_s: largest bucket one CTA sorts
-constexpr int kTargetBucket = 1024;               // aim for this final bucket size
+constexpr int kTargetBucket = 640;                // aim for this final bucket size
+                                                  // (mostly below the 1024-key class)
 constexpr int kSampleChunk = 4096;                // sample sort: pairs per CTA chunk
 constexpr int kDeepOversample = 16;               // samples per bucket at levels >= 2
 constexpr int kMaxLevels = 3;                     // partition levels before fallback
@@ -60,7 +61,7 @@ struct LevelSeg {
   uint32_t S;
   uint32_t nchunks;
   uint32_t nschunks;
-  uint32_t pad;
+  uint32_t nunits;      // histogram units: nchunks (CTA chunks) or 8 * nchunks (warp sub-chunks)
 };
 
 // A bucket handed to the in-SM sort.
@@ -109,6 +110,7 @@ struct LevelParams {
   uint64_t samp_cap, hist_cap, chunk_cap, seg_cap, final_cap, schunk_cap, bucket_cap;
   int level1_oversample;  // 1: a = 16 ceil(log2 k) for hinted k (the paper's rule)
   int classifier;         // 0: splitter tree, 1: leading-bits table
+  int warp_direct;        // 1: per-warp sub-chunks scattered straight to HBM
 };
 
 // Element source / destination of a level.

@@ -190,35 +190,54 @@ def test_full_size_2p28(ctx, name):
     torch.cuda.empty_cache()
 
 
-@pytest.fixture(scope="module")
-def ctx_table():
+CONFIGS = {
+    "tree_staged": {"classifier": 0, "warp_direct_max_k": 0},
+    "tree_warpdirect": {"classifier": 0, "warp_direct_max_k": 2048},
+    "table_warpdirect": {"classifier": 1, "warp_direct_max_k": 2048},
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CONFIGS))
+def ctx_cfg(request):
+    """A context with one non-default kernel configuration (tunables change
+    speed, never results)."""
     from paper_1606_08766_gb300 import Context
     c = Context(0)
-    c.set_tunable("classifier", 1)
-    assert c.get_tunable("classifier") == 1
+    for name, v in CONFIGS[request.param].items():
+        c.set_tunable(name, v)
+        assert c.get_tunable(name) == v
     yield c
     c.close()
 
 
 @pytest.mark.parametrize("name,k", PART_CASES)
-def test_partition_table_classifier_matches_oracle(ctx_table, oracle_mod, name, k):
+def test_partition_configs_match_oracle(ctx_cfg, oracle_mod, name, k):
     n = (1 << 17) + 1237
     keys = instances.generate(name, n, p=64, seed=7)
     ref = oracle_mod.partition(keys, k, seed=5)
-    ko, po, off = ctx_table.partition(_dev(keys), k, seed=5)
+    ko, po, off = ctx_cfg.partition(_dev(keys), k, seed=5)
     np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
     np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
     np.testing.assert_array_equal(_host_u64(ko), ref["keys_out"])
 
 
 @pytest.mark.parametrize("name", instances.NAMES)
-def test_sort_table_classifier_matches_oracle(ctx_table, oracle_mod, name):
+def test_sort_configs_match_oracle(ctx_cfg, oracle_mod, name):
     n = (1 << 20) + 77
     keys = instances.generate(name, n, p=64, seed=1)
     rk, rp = oracle_mod.sort(keys)
-    ko, po = ctx_table.sort(_dev(keys), p=64, seed=1)
+    ko, po = ctx_cfg.sort(_dev(keys), p=64, seed=1)
     np.testing.assert_array_equal(_host_u32(po), rp)
     np.testing.assert_array_equal(_host_u64(ko), rk)
+
+
+def test_configs_f64_segmented(ctx_cfg, oracle_mod):
+    keys, offs = instances.segmented_f64(700, 16, seed=31)
+    rk, rp = oracle_mod.segmented(keys, offs, oracle_mod.KEY_F64)
+    ko, po = ctx_cfg.segmented(torch.from_numpy(keys.view(np.float64).copy()).cuda(),
+                               torch.from_numpy(offs.view(np.int64)).cuda())
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint64), rk)
 
 
 def test_tunable_rejects_unknown(ctx):
