@@ -158,6 +158,70 @@ rsort_status rsort_partition_noalloc(rsort_key_type type, const void *d_keys_in,
                                      uint32_t *d_pos_out, uint64_t *d_offsets_out,
                                      void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of sort requests (no counterpart in the paper;
+ * the sorts are the same robust sample sort).
+ *
+ * rsort_submit queues a request and returns at once with a ticket.  A runtime
+ * thread of the context keeps up to `serve_slots` batches in flight on their
+ * own CUDA streams and scratch workspaces.  Requests of at most
+ * `serve_alone_min` keys (default 2^20) are grouped -- same key type, arrival
+ * order, up to `serve_batch_keys` keys -- and sorted together as the segments
+ * of one segmented sort; larger ones run alone.  A batch starts when a slot is
+ * free and its scratch fits the context's HBM budget next to the batches in
+ * flight, so requests arriving while others run are admitted as slots and
+ * memory free up and overlap with them on the device.  Each result is the
+ * same as sorting that request alone with rsort_sort (segment-local
+ * permutation), whatever it was batched with.
+ *
+ * The caller owns the request's device buffers; they must stay valid and
+ * untouched until the ticket reports a final status.  p_virtual only matters
+ * for requests that run alone (it does not change results).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    rsort_key_type type;
+    const void *d_keys_in;   /* n keys, must not alias d_keys_out            */
+    void *d_keys_out;        /* n keys                                       */
+    uint32_t *d_perm_out;    /* n positions                                  */
+    uint64_t n;              /* <= 2^32 - 1                                  */
+    uint32_t p_virtual;      /* 0/1: automatic; 2..2048                      */
+    uint64_t seed;
+} rsort_request;
+
+/* Queues a request.  *ticket_out identifies it.  Errors: EINVAL (bad
+ * arguments), ENOMEM (its scratch alone exceeds the context budget), ECUDA
+ * (the runtime could not start). */
+rsort_status rsort_submit(rsort_ctx *ctx, const rsort_request *req, uint64_t *ticket_out);
+
+/* Non-blocking status: RSORT_PENDING (queued or running), RSORT_OK (done;
+ * *latency_ns_out, if not NULL, gets submit-to-completion nanoseconds),
+ * RSORT_ECANCELLED, or the request's error.  EINVAL for an unknown ticket. */
+rsort_status rsort_poll(rsort_ctx *ctx, uint64_t ticket, uint64_t *latency_ns_out);
+
+/* Blocks until the request has a final status or timeout_ns passes
+ * (RSORT_ETIMEOUT).  Returns the final status otherwise. */
+rsort_status rsort_wait(rsort_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
+
+/* Cancels a request that has not started: RSORT_OK, its buffers are left
+ * untouched and its status becomes RSORT_ECANCELLED.  A running or finished
+ * request cannot be cancelled (RSORT_EINVAL). */
+rsort_status rsort_cancel(rsort_ctx *ctx, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, failed, queued;
+    uint32_t inflight_batches;
+    uint64_t batches;
+    uint64_t keys_completed;
+    double mean_batch_requests;
+    double p50_us, p99_us, max_us;   /* submit-to-completion latency */
+    double elapsed_s;                /* first submit to last completion */
+} rsort_serve_stats;
+
+/* Counters and latency percentiles since the runtime started (or the last
+ * reset).  All zero before the first submit. */
+rsort_status rsort_get_serve_stats(rsort_ctx *ctx, rsort_serve_stats *out);
+rsort_status rsort_reset_serve_stats(rsort_ctx *ctx);
+
 /* Profiling (tracing): when enabled, the library records CUDA events around
  * every kernel it launches on the call's stream.  rsort_phase_times copies up
  * to max entries of {kernel name, accumulated milliseconds, launches} into the
@@ -174,6 +238,8 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                1 (default): a lookup table over the keys' leading bits
  *                into the same sorted splitters, then a binary search inside
  *                the bin.
+ *   serve_slots, serve_batch_keys, serve_alone_min  serving runtime (see
+ *                rsort_submit); fixed once the runtime has started.
  *   warp_direct_max_k  partition levels with at most this many buckets per
  *                segment classify and scatter per warp sub-chunk straight to
  *                HBM; larger levels stage every sub-tile through shared

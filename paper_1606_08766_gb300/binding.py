@@ -37,6 +37,22 @@ class _Stats(ctypes.Structure):
                 ("bytes_moved", ctypes.c_uint64), ("level_elems", ctypes.c_uint64 * 4)]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("d_keys_in", ctypes.c_void_p),
+                ("d_keys_out", ctypes.c_void_p), ("d_perm_out", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("p_virtual", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("inflight_batches", ctypes.c_uint32),
+                ("batches", ctypes.c_uint64), ("keys_completed", ctypes.c_uint64),
+                ("mean_batch_requests", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double)]
+
+
 @dataclass
 class Stats:
     n: int
@@ -82,6 +98,12 @@ def load_library(build_if_missing: bool = True):
                                     ctypes.POINTER(ctypes.c_int)]),
         "rsort_launch_count": (i32, [vp, ctypes.POINTER(u64)]),
         "rsort_set_tunable": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
+        "rsort_submit": (i32, [vp, ctypes.POINTER(_Request), ctypes.POINTER(u64)]),
+        "rsort_poll": (i32, [vp, u64, ctypes.POINTER(u64)]),
+        "rsort_wait": (i32, [vp, u64, u64]),
+        "rsort_cancel": (i32, [vp, u64]),
+        "rsort_get_serve_stats": (i32, [vp, ctypes.POINTER(_ServeStats)]),
+        "rsort_reset_serve_stats": (i32, [vp]),
         "rsort_get_tunable": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
@@ -253,6 +275,39 @@ class Context:
         _check(self._lib.rsort_get_tunable(self._ctx, name.encode(), ctypes.byref(v)),
                "rsort_get_tunable")
         return v.value
+
+    # -- serving ----------------------------------------------------------
+    def submit(self, keys: torch.Tensor, keys_out: torch.Tensor, perm_out: torch.Tensor,
+               p: int = 0, seed: int = 1, key_type=None) -> int:
+        """Queues a sort request; the tensors must stay alive and untouched
+        until the ticket reports a final status."""
+        _check_keys(keys)
+        req = _Request(_key_type(keys, key_type), keys.data_ptr(), keys_out.data_ptr(),
+                       perm_out.data_ptr(), keys.numel(), p, seed & (2**64 - 1))
+        t = ctypes.c_uint64()
+        _check(self._lib.rsort_submit(self._ctx, ctypes.byref(req), ctypes.byref(t)),
+               "rsort_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(status, latency_ns); status 1 = pending, 0 = done."""
+        lat = ctypes.c_uint64(0)
+        st = self._lib.rsort_poll(self._ctx, ticket, ctypes.byref(lat))
+        return st, lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        return self._lib.rsort_wait(self._ctx, ticket, int(timeout_s * 1e9))
+
+    def cancel(self, ticket: int) -> int:
+        return self._lib.rsort_cancel(self._ctx, ticket)
+
+    def serve_stats(self) -> dict:
+        s = _ServeStats()
+        _check(self._lib.rsort_get_serve_stats(self._ctx, ctypes.byref(s)), "rsort_get_serve_stats")
+        return {name: getattr(s, name) for name, _ in _ServeStats._fields_}
+
+    def reset_serve_stats(self):
+        _check(self._lib.rsort_reset_serve_stats(self._ctx), "rsort_reset_serve_stats")
 
     def launch_count(self) -> int:
         v = ctypes.c_uint64()

@@ -15,6 +15,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "engine.h"
 #include "rsort_internal.cuh"
 
 namespace rsort {
@@ -22,54 +23,43 @@ namespace rsort {
 // ---------------------------------------------------------------------------
 // Kernel timer: a pair of CUDA events around every launch, resolved lazily.
 // ---------------------------------------------------------------------------
-struct TimerImpl {
-  struct Rec {
-    const char* name;
-    cudaEvent_t a, b;
-  };
-  std::vector<Rec> open;
-  std::vector<cudaEvent_t> pool;
-  std::unordered_map<std::string, std::pair<double, uint64_t>> acc;
-  std::vector<std::string> order;
-  const char* pending = nullptr;
-  cudaEvent_t pending_ev = nullptr;
-
-  cudaEvent_t get() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
+cudaEvent_t TimerImpl::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
     return e;
   }
-  void resolve() {
-    for (auto& r : open) {
-      cudaEventSynchronize(r.b);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, r.a, r.b);
-      auto it = acc.find(r.name);
-      if (it == acc.end()) {
-        order.push_back(r.name);
-        acc[r.name] = {ms, 1};
-      } else {
-        it->second.first += ms;
-        it->second.second += 1;
-      }
-      pool.push_back(r.a);
-      pool.push_back(r.b);
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void TimerImpl::resolve() {
+  for (auto& r : open) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto it = acc.find(r.name);
+    if (it == acc.end()) {
+      order.push_back(r.name);
+      acc[r.name] = {ms, 1};
+    } else {
+      it->second.first += ms;
+      it->second.second += 1;
     }
-    open.clear();
+    pool.push_back(r.a);
+    pool.push_back(r.b);
   }
-  ~TimerImpl() {
-    for (auto& r : open) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
+  open.clear();
+}
+
+TimerImpl::~TimerImpl() {
+  for (auto& r : open) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
   }
-};
+  for (auto e : pool) cudaEventDestroy(e);
+}
 
 void KernelTimer::begin(const char* name, cudaStream_t s) {
   TimerImpl* t = (TimerImpl*)impl;
@@ -83,32 +73,6 @@ void KernelTimer::end(cudaStream_t s) {
   cudaEventRecord(b, s);
   t->open.push_back({t->pending, t->pending_ev, b});
 }
-
-}  // namespace rsort
-
-using namespace rsort;
-
-struct rsort_ctx {
-  int device = 0;
-  int num_sms = 0;
-  uint64_t budget = 0;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  cudaStream_t last_stream = nullptr;
-  rsort_status latched = RSORT_OK;
-  DevState* h_state = nullptr;  // pinned read-back buffer
-  uint64_t launches = 0;
-  bool profiling = false;
-  // tunable "classifier": 0 splitter tree, 1 leading-bits table (default: the
-  // table; both give the same buckets and the table measured faster on GB300)
-  int classifier = 1;
-  // tunable "warp_direct_max_k": warp-direct kernels up to this k (default off:
-  // direct scattered stores measured ~3x slower than shared-memory combining)
-  int wd_max_k = 0;
-  KernelTimer timer;
-  TimerImpl timer_impl;
-  std::mutex mu;
-};
 
 namespace {
 
@@ -254,27 +218,9 @@ rsort_status cuda_status(rsort_ctx* c) {
   return latch(c, RSORT_ECUDA);
 }
 
-rsort_status ensure_arena(rsort_ctx* c, size_t bytes, cudaStream_t s) {
-  if (bytes <= c->arena_bytes) return RSORT_OK;
-  if (c->budget && bytes > c->budget) return RSORT_ENOMEM;
-  if (c->arena) {
-    cudaFreeAsync(c->arena, s);
-    c->arena = nullptr;
-    c->arena_bytes = 0;
-  }
-  void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
-    cudaGetLastError();
-    return RSORT_ENOMEM;
-  }
-  c->arena = p;
-  c->arena_bytes = bytes;
-  return RSORT_OK;
-}
-
 template <typename T>
-T* at(rsort_ctx* c, size_t off) {
-  return reinterpret_cast<T*>(static_cast<unsigned char*>(c->arena) + off);
+T* at(Workspace& ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(ws.arena) + off);
 }
 
 // Kernel attributes (dynamic shared memory limits) are set once per device,
@@ -292,7 +238,7 @@ void set_attributes_once(int device) {
 
 // Enqueues the partition levels and the in-SM sort after the level-1 list and
 // the directly sortable items have been initialised.
-void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, DevState* st,
+void enqueue_levels_and_local(rsort_ctx* c, Workspace& ws, const Plan& p, const LaunchEnv& e, DevState* st,
                               FinalItem* items, SegIn* const lists[2], rsort_key_type type,
                               const void* d_keys_in, const Dst& out, const Dst& tmp,
                               uint64_t seed, uint32_t k1) {
@@ -308,10 +254,10 @@ void enqueue_levels_and_local(rsort_ctx* c, const Plan& p, const LaunchEnv& e, D
     }
     const Dst& dst = (L & 1) ? tmp : out;
     const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
-    launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(c, p.off_segs), src,
-                 dst, where, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
-                 at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
-                 at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums), items, kmax,
+    launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(ws, p.off_segs), src,
+                 dst, where, at<uint64_t>(ws, p.off_samp_key), at<uint32_t>(ws, p.off_samp_idx),
+                 at<uint64_t>(ws, p.off_ssamp_key), at<uint32_t>(ws, p.off_ssamp_idx),
+                 at<uint32_t>(ws, p.off_hist), at<uint32_t>(ws, p.off_sums), items, kmax,
                  L == p.levels, 1, nullptr, p.n, 0);
   }
   launch_local_sort(e, st, items, p.final_cap, (const uint64_t*)d_keys_in, out, tmp,
@@ -329,9 +275,30 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->wd_max_k = (int)v;
     return RSORT_OK;
   }
+  if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
+  if (strcmp(name, "serve_slots") == 0) {
+    if (v < 1 || v > 8) return RSORT_EINVAL;
+    c->serve_slots = (int)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_batch_keys") == 0) {
+    if (v < 1 || v > (1ll << 30)) return RSORT_EINVAL;
+    c->serve_batch_keys = (uint64_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_alone_min") == 0) {
+    if (v < 0 || v > 0xFFFFFFFFll) return RSORT_EINVAL;
+    c->serve_alone_min = (uint64_t)v;
+    return RSORT_OK;
+  }
   return RSORT_EINVAL;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Engine (engine.h): workspaces and whole-sort enqueue functions
+// ---------------------------------------------------------------------------
 LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   LaunchEnv e;
   e.stream = s;
@@ -341,7 +308,124 @@ LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   return e;
 }
 
+
+rsort_status ensure_workspace(rsort_ctx* c, Workspace& ws, size_t bytes, cudaStream_t s) {
+  if (bytes <= ws.bytes) return RSORT_OK;
+  std::lock_guard<std::mutex> lk(c->alloc_mu);
+  const uint64_t others = c->held.load() - ws.bytes;
+  if (c->budget && others + bytes > c->budget) return RSORT_ENOMEM;
+  if (ws.arena) {
+    cudaFreeAsync(ws.arena, s);
+    c->held -= ws.bytes;
+    ws.arena = nullptr;
+    ws.bytes = 0;
+  }
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return RSORT_ENOMEM;
+  }
+  ws.arena = p;
+  ws.bytes = bytes;
+  c->held += bytes;
+  return RSORT_OK;
+}
+
+void release_workspace(rsort_ctx* c, Workspace& ws, cudaStream_t s) {
+  if (!ws.arena) return;
+  std::lock_guard<std::mutex> lk(c->alloc_mu);
+  if (s) cudaFreeAsync(ws.arena, s);
+  else cudaFree(ws.arena);
+  c->held -= ws.bytes;
+  ws.arena = nullptr;
+  ws.bytes = 0;
+}
+
+namespace {
+
+Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
+  Plan p;
+  p.classifier = c->classifier;
+  p.wd_max_k = c->wd_max_k;
+  const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
+  if (n <= (uint64_t)kBucketCap) {
+    p.n = n;
+    p.direct = 1;
+    p.final_cap = 4;
+    p.seg_cap = 1;
+    p.need_tmp = false;
+    p.levels = 0;
+  } else {
+    plan_levels(p, n, k1, 1, c->num_sms, kMaxLevels);
+    p.need_tmp = true;
+  }
+  layout(p);
+  return p;
+}
+
+Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
+  Plan p;
+  p.classifier = c->classifier;
+  p.wd_max_k = c->wd_max_k;
+  const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
+  plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
+  p.final_cap += num_segments;
+  p.need_tmp = true;
+  layout(p);
+  return p;
+}
+
 }  // namespace
+
+size_t sort_scratch_bytes(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
+  return n == 0 ? 0 : plan_sort(c, n, p_virtual).total;
+}
+
+size_t segmented_scratch_bytes(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
+  return (n == 0 || num_segments == 0) ? 0 : plan_segmented(c, n, num_segments).total;
+}
+
+rsort_status enqueue_sort(rsort_ctx* c, Workspace& ws, const LaunchEnv& e, rsort_key_type type,
+                          const void* d_keys_in, void* d_keys_out, uint32_t* d_perm_out,
+                          uint64_t n, uint32_t p_virtual, uint64_t seed, DevState** st_out) {
+  Plan p = plan_sort(c, n, p_virtual);
+  const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
+  rsort_status rs = ensure_workspace(c, ws, p.total, e.stream);
+  if (rs != RSORT_OK) return rs;
+  DevState* st = at<DevState>(ws, p.off_state);
+  FinalItem* items = at<FinalItem>(ws, p.off_items);
+  SegIn* lists[2] = {at<SegIn>(ws, p.off_list0), at<SegIn>(ws, p.off_list1)};
+  launch_init_plain(e, st, lists[1], items, n, k1, p.direct, p.final_cap);
+  Dst out{(uint64_t*)d_keys_out, d_perm_out};
+  Dst tmp{at<uint64_t>(ws, p.off_tmp_key), at<uint32_t>(ws, p.off_tmp_idx)};
+  enqueue_levels_and_local(c, ws, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, k1);
+  if (st_out) *st_out = st;
+  return RSORT_OK;
+}
+
+rsort_status enqueue_segmented(rsort_ctx* c, Workspace& ws, const LaunchEnv& e,
+                               rsort_key_type type, const void* d_keys_in, void* d_keys_out,
+                               uint32_t* d_perm_out, uint64_t n, const uint64_t* d_offsets,
+                               uint32_t num_segments, uint64_t seed, DevState** st_out) {
+  Plan p = plan_segmented(c, n, num_segments);
+  rsort_status rs = ensure_workspace(c, ws, p.total, e.stream);
+  if (rs != RSORT_OK) return rs;
+  DevState* st = at<DevState>(ws, p.off_state);
+  FinalItem* items = at<FinalItem>(ws, p.off_items);
+  SegIn* lists[2] = {at<SegIn>(ws, p.off_list0), at<SegIn>(ws, p.off_list1)};
+  launch_init_plain(e, st, lists[1], items, 0, 0, 0, p.final_cap);  // reset the control block
+  launch_init_segments(e, st, d_offsets, num_segments, n, lists[1], items, p.seg_cap,
+                       p.final_cap);
+  Dst out{(uint64_t*)d_keys_out, d_perm_out};
+  Dst tmp{at<uint64_t>(ws, p.off_tmp_key), at<uint32_t>(ws, p.off_tmp_idx)};
+  enqueue_levels_and_local(c, ws, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, 0);
+  if (st_out) *st_out = st;
+  return RSORT_OK;
+}
+
+}  // namespace rsort
+
+using namespace rsort;
 
 extern "C" {
 
@@ -410,8 +494,9 @@ rsort_status rsort_destroy(rsort_ctx* c) {
   if (!c) return RSORT_OK;
   {
     DeviceGuard g(c->device);
+    destroy_server(c);
     cudaDeviceSynchronize();
-    if (c->arena) cudaFree(c->arena);
+    release_workspace(c, c->ws, nullptr);
     if (c->h_state) cudaFreeHost(c->h_state);
     cudaGetLastError();
   }
@@ -425,14 +510,14 @@ rsort_status rsort_check(rsort_ctx* c) {
   DeviceGuard g(c->device);
   if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) latch(c, RSORT_ECUDA);
   cuda_status(c);
-  if (c->arena) {
+  if (c->ws.arena) {
     DevState st;
-    if (cudaMemcpy(&st, c->arena, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(&st, c->ws.arena, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) {
       latch(c, RSORT_ECUDA);
     } else if (st.error) {
       latch(c, RSORT_EDEVICE);
       // the error is reported once: clear the device word
-      cudaMemset(static_cast<unsigned char*>(c->arena) + offsetof(DevState, error), 0,
+      cudaMemset(static_cast<unsigned char*>(c->ws.arena) + offsetof(DevState, error), 0,
                  sizeof(uint32_t));
     }
   }
@@ -472,19 +557,20 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   p.final_cap = 4;
   p.need_tmp = false;
   layout(p);
-  rsort_status rs = ensure_arena(c, p.total, s);
+  Workspace& ws = c->ws;
+  rsort_status rs = ensure_workspace(c, ws, p.total, s);
   if (rs != RSORT_OK) return latch(c, rs);
-  DevState* st = at<DevState>(c, p.off_state);
-  SegIn* list1 = at<SegIn>(c, p.off_list1);
-  launch_init_plain(e, st, list1, at<FinalItem>(c, p.off_items), n, k, 0, p.final_cap);
+  DevState* st = at<DevState>(ws, p.off_state);
+  SegIn* list1 = at<SegIn>(ws, p.off_list1);
+  launch_init_plain(e, st, list1, at<FinalItem>(ws, p.off_items), n, k, 0, p.final_cap);
   LevelParams P = level_params(p, 1, seed, (int)kk);
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
-  launch_level(e, P, st, list1, at<SegIn>(c, p.off_list0), at<LevelSeg>(c, p.off_segs), src, dst,
-               kWhereOut, at<uint64_t>(c, p.off_samp_key), at<uint32_t>(c, p.off_samp_idx),
-               at<uint64_t>(c, p.off_ssamp_key), at<uint32_t>(c, p.off_ssamp_idx),
-               at<uint32_t>(c, p.off_hist), at<uint32_t>(c, p.off_sums),
-               at<FinalItem>(c, p.off_items), (int)kk, 1, 0, d_offsets_out, n,
+  launch_level(e, P, st, list1, at<SegIn>(ws, p.off_list0), at<LevelSeg>(ws, p.off_segs), src,
+               dst, kWhereOut, at<uint64_t>(ws, p.off_samp_key), at<uint32_t>(ws, p.off_samp_idx),
+               at<uint64_t>(ws, p.off_ssamp_key), at<uint32_t>(ws, p.off_ssamp_idx),
+               at<uint32_t>(ws, p.off_hist), at<uint32_t>(ws, p.off_sums),
+               at<FinalItem>(ws, p.off_items), (int)kk, 1, 0, d_offsets_out, n,
                type == RSORT_KEY_F64);
   return cuda_status(c);
 }
@@ -507,31 +593,12 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
   if (opt_stats) memset(opt_stats, 0, sizeof(*opt_stats));
   if (n == 0) return RSORT_OK;
   LaunchEnv e = env_of(c, s);
-  Plan p;
-  p.classifier = c->classifier;
-  p.wd_max_k = c->wd_max_k;
   const int direct = n <= (uint64_t)kBucketCap;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
-  if (direct) {
-    p.n = n;
-    p.final_cap = 4;
-    p.seg_cap = 1;
-    p.need_tmp = false;
-  } else {
-    plan_levels(p, n, k1, 1, c->num_sms, kMaxLevels);
-    p.need_tmp = true;
-  }
-  layout(p);
-  rsort_status rs = ensure_arena(c, p.total, s);
+  DevState* st = nullptr;
+  rsort_status rs = enqueue_sort(c, c->ws, e, type, d_keys_in, d_keys_out, d_perm_out, n,
+                                 p_virtual, seed, &st);
   if (rs != RSORT_OK) return latch(c, rs);
-  DevState* st = at<DevState>(c, p.off_state);
-  FinalItem* items = at<FinalItem>(c, p.off_items);
-  SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
-  launch_init_plain(e, st, lists[1], items, n, k1, direct, p.final_cap);
-  Dst out{(uint64_t*)d_keys_out, d_perm_out};
-  Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
-  if (direct) p.levels = 0;
-  enqueue_levels_and_local(c, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, k1);
   rs = cuda_status(c);
   if (rs != RSORT_OK) return rs;
   if (opt_stats) {
@@ -581,25 +648,9 @@ rsort_status rsort_segmented(rsort_ctx* c, rsort_key_type type, const void* d_ke
   c->last_stream = s;
   if (n == 0 || num_segments == 0) return RSORT_OK;
   LaunchEnv e = env_of(c, s);
-  Plan p;
-  p.classifier = c->classifier;
-  p.wd_max_k = c->wd_max_k;
-  const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
-  plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
-  p.final_cap += num_segments;
-  p.need_tmp = true;
-  layout(p);
-  rsort_status rs = ensure_arena(c, p.total, s);
+  rsort_status rs = enqueue_segmented(c, c->ws, e, type, d_keys_in, d_keys_out, d_perm_out, n,
+                                      d_offsets, num_segments, seed, nullptr);
   if (rs != RSORT_OK) return latch(c, rs);
-  DevState* st = at<DevState>(c, p.off_state);
-  FinalItem* items = at<FinalItem>(c, p.off_items);
-  SegIn* lists[2] = {at<SegIn>(c, p.off_list0), at<SegIn>(c, p.off_list1)};
-  launch_init_plain(e, st, lists[1], items, 0, 0, 0, p.final_cap);  // reset the control block
-  launch_init_segments(e, st, d_offsets, num_segments, n, lists[1], items, p.seg_cap,
-                       p.final_cap);
-  Dst out{(uint64_t*)d_keys_out, d_perm_out};
-  Dst tmp{at<uint64_t>(c, p.off_tmp_key), at<uint32_t>(c, p.off_tmp_idx)};
-  enqueue_levels_and_local(c, p, e, st, items, lists, type, d_keys_in, out, tmp, seed, 0);
   return cuda_status(c);
 }
 
@@ -652,6 +703,18 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "warp_direct_max_k") == 0) {
     *value = c->wd_max_k;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_slots") == 0) {
+    *value = c->serve_slots;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_batch_keys") == 0) {
+    *value = (int64_t)c->serve_batch_keys;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_alone_min") == 0) {
+    *value = (int64_t)c->serve_alone_min;
     return RSORT_OK;
   }
   return RSORT_EINVAL;
