@@ -30,7 +30,8 @@ N_KEYS = 1 << 28
 P_VIRTUAL = 1024
 WORKLOAD = "Uniform uint64 keys, n=2^28, p=1024 virtual partitions, seed 1"
 METRIC = "GKeys/s"
-CPU_SAMPLE = 1 << 24
+CPU_SAMPLE = 1 << 24   # cpu_baseline leg: 3 runs of this many keys
+REF_SAMPLE = 1 << 22   # --impl reference: keys per step
 
 # algorithmic HBM bytes per key of each kernel's input (8 B key, 4 B position)
 ALGO_BYTES_PER_KEY = {
@@ -41,6 +42,16 @@ ALGO_BYTES_PER_KEY = {
     "L3.classify": 8,
     "L3.scatter": 24,
     "local_sort": 24,       # read + write (key, position)
+}
+
+
+# DRAM bytes (read + write) per input key of a kernel, from one ncu capture of
+# the current kernel code on a smaller case of the same workload (traffic
+# grows in proportion to the keys; the capture and command are summarised in
+# profiles/).  Remove an entry whenever its kernel changes.
+MEASURED_TRAFFIC_PER_KEY = {
+    # k_scatter, level 1 (k = 1024), n = 2^26: 1.301 GB read + 1.719 GB written
+    "L1.scatter": (1.301148e9 + 1.719255e9) / (1 << 26),
 }
 
 
@@ -110,6 +121,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's value (weak scaling: every rank sorts its own
+    instance and the job takes as long as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gkeys(keys_per_rank: int, world: int, ms_step: float) -> float:
+    """Keys sorted by all ranks per second of the slowest rank, in GKeys/s."""
+    return keys_per_rank * world / (ms_step / 1e3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -130,16 +157,16 @@ def run_reference(args):
     keys = instances.generate("uniform", N_KEYS, p=P_VIRTUAL, seed=1)
     times = []
     for step in range(args.warmup + args.steps):
-        lo = (step * CPU_SAMPLE) % (N_KEYS - CPU_SAMPLE)
-        sample = np.ascontiguousarray(keys[lo:lo + CPU_SAMPLE])
+        lo = (step * REF_SAMPLE) % (N_KEYS - REF_SAMPLE)
+        sample = np.ascontiguousarray(keys[lo:lo + REF_SAMPLE])
         t0 = time.perf_counter()
         oracle.sort(sample)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
     ms = 1e3 * statistics.mean(times)
-    value = CPU_SAMPLE / (ms / 1e3) / 1e9
-    sample_desc = f"{CPU_SAMPLE} consecutive keys of the 2^28 Uniform input per step"
+    value = REF_SAMPLE / (ms / 1e3) / 1e9
+    sample_desc = f"{REF_SAMPLE} consecutive keys of the 2^28 Uniform input per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -168,6 +195,164 @@ def cpu_baseline_leg():
     v = CPU_SAMPLE / statistics.median(ts) / 1e9
     return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"first {CPU_SAMPLE} keys of the Uniform instance, 3 runs, median"}
+
+
+def batched_leg(ctx, dev, nseg=100_000, maxlog=15, plain_subset=20_000):
+    """Batched segmented sort of float64 segments (log-uniform sizes, 10%
+    duplicates) in one launch sequence, against one plain rsort_sort per
+    segment on a subset of the same segments."""
+    import numpy as np
+    import torch
+
+    import instances
+
+    keys, offs = instances.segmented_f64(nseg, maxlog, seed=1)
+    n = int(keys.shape[0])
+    x = torch.from_numpy(keys.view(np.float64)).to(dev)
+    o = torch.from_numpy(offs.view(np.int64)).to(dev)
+    ko = torch.empty_like(x)
+    po = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        ctx.segmented(x, o, keys_out=ko, perm_out=po)
+    torch.cuda.synchronize(dev)
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.segmented(x, o, keys_out=ko, perm_out=po)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batched = e0.elapsed_time(e1) / reps
+    # the same launch sequence captured once in a CUDA graph and replayed
+    side = torch.cuda.Stream(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        ctx.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.graph(g, stream=side):
+        ctx.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
+    g.replay()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_graph = e0.elapsed_time(e1) / reps
+    # one plain sort per segment (pointer-level calls, same stream)
+    m = int(offs[plain_subset])
+    ko2 = torch.empty(m, dtype=torch.float64, device=dev)
+    po2 = torch.empty(m, dtype=torch.int32, device=dev)
+    xp, kp, pp, sh = x.data_ptr(), ko2.data_ptr(), po2.data_ptr(), stream.cuda_stream
+    offs_l = [int(v) for v in offs[: plain_subset + 1]]
+
+    def plain_pass():
+        for s in range(plain_subset):
+            a, b = offs_l[s], offs_l[s + 1]
+            ctx.sort_raw(1, xp + 8 * a, kp + 8 * a, pp + 4 * a, b - a, 1, 1, sh)
+
+    plain_pass()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = e0.elapsed_time(e1)
+    wall_plain = time.perf_counter() - t0
+    same = bool(torch.equal(ko2, ko[:m])) and bool(torch.equal(po2, po[:m]))
+    gk = lambda keys_, ms_: keys_ / (ms_ / 1e3) / 1e9
+    plain_gk = m / max(wall_plain, ms_plain / 1e3) / 1e9
+    return {"workload": f"{offs.shape[0] - 1} float64 segments, sizes floor(exp(U ln 2^{maxlog})), "
+                        f"10% duplicates, {n} keys",
+            "keys": n, "segments": int(offs.shape[0] - 1),
+            "batched_gkeys_s": gk(n, ms_batched), "batched_ms": ms_batched,
+            "graph_replay_gkeys_s": gk(n, ms_graph),
+            "plain_per_segment_gkeys_s": plain_gk,
+            "plain_subset": f"first {plain_subset} segments ({m} keys), one rsort_sort each",
+            "speedup_vs_plain": gk(n, ms_batched) / plain_gk,
+            "identical_to_plain": same}
+
+
+def serving_leg(dev, requests=2000, lo_log2=4, hi_log2=20, seed=5):
+    """Continuous batching under the serving runtime against serial plain
+    sorts of the same requests, plus latency under Poisson arrivals."""
+    import math
+    import random
+
+    import numpy as np
+    import torch
+
+    import instances
+    from paper_1606_08766_gb300 import Context
+
+    rng = random.Random(seed)
+    sizes = [int(math.exp(rng.uniform(lo_log2 * math.log(2), hi_log2 * math.log(2))))
+             for _ in range(requests)]
+    reqs = []
+    for i, n in enumerate(sizes):
+        name = instances.NAMES[i % len(instances.NAMES)]
+        k = instances.generate(name, n, p=16, seed=seed + i)
+        if i % 2:
+            t = torch.from_numpy(k.view(np.int64)).to(dev)
+            kt = 0
+        else:
+            t = torch.from_numpy(k.astype(np.float64) - 2.0 ** 63).to(dev)
+            kt = 1
+        reqs.append((t, torch.empty_like(t), torch.empty(n, dtype=torch.int32, device=dev), kt))
+    total = sum(sizes)
+    torch.cuda.synchronize(dev)
+    ctx = Context(dev.index)
+    # warm-up: every request once through the server
+    ts = [ctx.submit(t, o, p, key_type=kt) for t, o, p, kt in reqs]
+    for t in ts:
+        ctx.wait(t, 300)
+    ctx.reset_serve_stats()
+    # capacity: everything offered at once
+    t0 = time.perf_counter()
+    ts = [ctx.submit(t, o, p, key_type=kt) for t, o, p, kt in reqs]
+    for t in ts:
+        assert ctx.wait(t, 300) == 0
+    wall = time.perf_counter() - t0
+    sat = ctx.serve_stats()
+    # serial plain sorts, one rsort_sort per request on one stream
+    stream = torch.cuda.current_stream(dev)
+    plain = Context(dev.index)
+    for t, o, p, kt in reqs[:50]:
+        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), p.data_ptr(), t.numel(), 1, 1,
+                       stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for t, o, p, kt in reqs:
+        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), p.data_ptr(), t.numel(), 1, 1,
+                       stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    wall_plain = time.perf_counter() - t0
+    plain.close()
+    # latency under Poisson arrivals at half the measured capacity
+    rate = 0.5 * requests / wall
+    ctx.reset_serve_stats()
+    ts = []
+    t_next = time.perf_counter()
+    for t, o, p, kt in reqs:
+        t_next += rng.expovariate(rate)
+        while time.perf_counter() < t_next:
+            pass
+        ts.append(ctx.submit(t, o, p, key_type=kt))
+    for t in ts:
+        assert ctx.wait(t, 300) == 0
+    poi = ctx.serve_stats()
+    ctx.close()
+    return {"workload": f"{requests} requests, sizes log-uniform in [2^{lo_log2}, 2^{hi_log2}], "
+                        f"u64/f64 alternating over the 11 instances, {total} keys",
+            "served_requests_s": requests / wall, "served_gkeys_s": total / wall / 1e9,
+            "plain_serial_requests_s": requests / wall_plain,
+            "plain_serial_gkeys_s": total / wall_plain / 1e9,
+            "speedup_vs_plain": wall_plain / wall,
+            "saturated_p50_us": sat["p50_us"], "saturated_p99_us": sat["p99_us"],
+            "mean_batch_requests": sat["mean_batch_requests"],
+            "poisson_rate_requests_s": rate, "p50_us": poi["p50_us"], "p99_us": poi["p99_us"]}
 
 
 def run_rsort(args):
@@ -231,12 +416,8 @@ def run_rsort(args):
     phases = ctx.phase_times()
     ctx.set_profiling(False)
     ctx.check()
-    ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = (n * ws) / (ms_step / 1e3) / 1e9
+    ms_step = max_over_ranks(ms_total / args.steps, dist, dev)
+    value = whole_job_gkeys(n, ws, ms_step)
 
     # -- per-kernel roofline (dominant kernel)
     _, _, st = ctx.sort(keys, p=P_VIRTUAL, seed=1, keys_out=keys_out, perm_out=perm, stats=True)
@@ -256,9 +437,11 @@ def run_rsort(args):
         kernels[name] = info
     dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["ms_per_launch"]
               * kernels[k]["launches"])
+    traffic = MEASURED_TRAFFIC_PER_KEY.get(dom)
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak,
             "unit": "GB/s", "frac": kernels[dom]["gbs"] / peak, "peak_kind": peak_kind,
-            "traffic": None}
+            "algo_bytes_per_launch": kernels[dom]["algo_bytes"],
+            "traffic": traffic * elems.get(dom.split(".")[0], n) if traffic else None}
 
     # -- end-to-end through the C ABI with host buffers (pinned), copies timed
     keys_pin = torch.from_numpy(keys_h.view(np.int64)).pin_memory()
@@ -278,15 +461,17 @@ def run_rsort(args):
         perm_pin.copy_(perm, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
     e2e = {"value": (n * ws) / (e2e_ms / 1e3) / 1e9, "unit": METRIC,
            "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + n * 4}
 
     cpu = cpu_baseline_leg() if (rank == 0 and ws == 1) else None
+    extra = {}
+    if rank == 0 and ws == 1 and not args.skip_systems:
+        del keys_pin, out_pin, perm_pin
+        extra["batched"] = batched_leg(ctx, dev)
+        torch.cuda.empty_cache()
+        extra["serving"] = serving_leg(dev)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
@@ -300,7 +485,7 @@ def run_rsort(args):
                        "max_over_mean": st.max_over_mean, "levels": st.levels,
                        "tunables": {"classifier": ctx.get_tunable("classifier")}},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "kernels": kernels,
+            "gpu_launches": launches, "kernels": kernels, **extra,
         }))
     ctx.close()
     if dist:
@@ -313,6 +498,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsort", choices=["rsort", "reference"])
+    ap.add_argument("--skip-systems", action="store_true",
+                    help="skip the batched-segmented and serving legs")
     ap.add_argument("--tunable", action="append", default=[],
                     help="name=value tunable of the library context (repeatable)")
     ap.add_argument("--n", type=int, default=N_KEYS,
