@@ -10,7 +10,8 @@
 //                       Ranking", all in one CTA)
 //   otherwise           split the bucket's key range [min, max] into ~2m
 //                       equal-width bins (a counting sort in shared memory),
-//                       then rank-by-counting inside each bin; the bins of a
+//                       then rank by counting inside each bin (an element
+//                       alone in its bin is already in place); the bins of a
 //                       bucket are tiny unless its keys cluster
 //   a crowded bin       bitonic sort of the whole bucket (Appendix "Bitonic
 //   (> kBinLimit)       Sort"), which needs no assumption on the keys
@@ -23,7 +24,7 @@
 
 namespace rsort {
 
-constexpr int kBinLimit = 32;
+constexpr int kBinLimit = 16;
 static_assert(kRankMax <= kLocalThreads, "rank-by-counting holds one element per thread");
 
 struct CtaSortSmem {
@@ -123,10 +124,10 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   }
   __syncthreads();
   // exclusive scan of the nb 16-bit counters (nb/2 words; each thread a run)
+  const uint32_t words = nb / 2;
+  const uint32_t per = (words + NT - 1) / NT;
+  const uint32_t w0 = tid * per;
   {
-    const uint32_t words = nb / 2;
-    const uint32_t per = (words + NT - 1) / NT;
-    const uint32_t w0 = tid * per;
     uint32_t loc = 0;
     for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
       const uint32_t v = s.hist[w];
@@ -174,26 +175,35 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
   }
   __syncthreads();
-  // rank by counting inside each bin
+  // rank by counting inside each bin; an element alone in its bin is final
+  constexpr uint32_t kInPlace = 0xffffffffu;
   uint32_t fin[ITEMS];
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
+    fin[r] = kInPlace;
     if (r * NT + tid < m) {
       const uint32_t b = bs[r] >> 16;
       const uint32_t lo = bin_start(s.hist, b);
       const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
-      uint32_t rank = 0;
-      for (uint32_t q = lo; q < hi; ++q) rank += pair_less(s.k[q], s.i[q], key[r], idx[r]) ? 1u : 0u;
-      fin[r] = lo + rank;
+      if (hi - lo > 1) {
+        uint32_t rank = 0;
+        for (uint32_t q = lo; q < hi; ++q)
+          rank += pair_less(s.k[q], s.i[q], key[r], idx[r]) ? 1u : 0u;
+        fin[r] = lo + rank;
+      }
     }
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
-    if (r * NT + tid < m) { s.k[fin[r]] = key[r]; s.i[fin[r]] = idx[r]; }
+    if (fin[r] != kInPlace) {
+      s.k[fin[r]] = key[r];
+      s.i[fin[r]] = idx[r];
+    }
   }
   __syncthreads();
   (void)kCap;
+  (void)w0;
 }
 
 }  // namespace rsort

@@ -701,6 +701,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
     return r;
   };
   const uint64_t pol = l2_evict_first_policy();
+  const uint64_t pol_keep = l2_evict_last_policy();
   const uint64_t total = st->total_chunks;
   const uint32_t G = st->cur_nseg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -816,8 +817,8 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         const uint32_t b = B.b[q];
         const uint64_t d = (uint64_t)sm.hist[b] + (q - sm.sbase[b]);
         const uint64_t kv = B.key[q];
-        dst.key[d] = unmap_out ? ordered_to_f64(kv) : kv;
-        dst.idx[d] = B.idx[q];
+        st_keep_u64(dst.key + d, unmap_out ? ordered_to_f64(kv) : kv, pol_keep);
+        st_keep_u32(dst.idx + d, B.idx[q], pol_keep);
       }
       __syncthreads();
       for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
