@@ -332,6 +332,9 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       s.nchunks = nch;
       s.nschunks = nsch;
       s.nunits = nch * (P.warp_direct ? kPartWarps : 1);
+      // equal chunks inside the segment (the level's W bounds their size)
+      s.W = nch ? (uint32_t)(((uint64_t)in.m + nch - 1) / nch) : P.W;
+      s.pad = 0;
       segs[g] = s;
     }
     __syncthreads();
@@ -387,10 +390,10 @@ k_sample(const DevState* st, const LevelSeg* segs, Src src, uint64_t* samp_key,
 // Step 2a: sort chunks of up to kSampleChunk sample pairs in one CTA each
 // (cta_sort_pairs).  Single-chunk samples go straight to the sorted-sample
 // array.  Samples of a segment are drawn in position order.
-__global__ void __launch_bounds__(kLocalThreads)
+__global__ void __launch_bounds__(kSampleThreads, 1)
 k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_key,
                      uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
-  constexpr int NT = kLocalThreads, IT = kSampleChunk / kLocalThreads;
+  constexpr int NT = kSampleThreads, IT = kSampleChunk / kSampleThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSortSmem s;
   s.k = (uint64_t*)smem_raw;
@@ -560,8 +563,8 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
     }
     for (uint32_t b = threadIdx.x; b < sg.k; b += kPartThreads) sm.hist[b] = 0;
     const uint64_t cl = c - sg.chunk_off;
-    const uint64_t cs = sg.start + cl * W;
-    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
     const uint64_t nst = (ce - cs + kCT - 1) / kCT;
     auto issue = [&](uint64_t s) {
       if (s < nst) {
@@ -721,8 +724,8 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
     const uint64_t cl = c - sg.chunk_off;
     for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
       sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] + sg.delta);
-    const uint64_t cs = sg.start + cl * W;
-    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
     const uint64_t nst = (ce - cs + kST - 1) / kST;
     auto issue = [&](uint64_t s) {
       if (s < nst) {
@@ -898,8 +901,8 @@ k_classify_count_wd(const DevState* st, const LevelSeg* segs, Src src, const uin
     const uint32_t k = sg.k;
     for (uint32_t b = lane; b < k; b += 32) row[b] = 0;
     const uint64_t cl = c - sg.chunk_off;
-    const uint64_t cs = sg.start + cl * W;
-    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
     uint64_t ws, we;
     warp_subchunk(cs, ce, warp, ws, we);
     const uint64_t nsteps = (we - ws + kWdKeys - 1) / kWdKeys;
@@ -979,8 +982,8 @@ k_scatter_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* 
     for (uint32_t b = lane; b < k; b += 32)
       row[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl * kPartWarps +
                                     warp] + sg.delta);
-    const uint64_t cs = sg.start + cl * W;
-    const uint64_t ce = umin64(cs + W, sg.start + sg.m);
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
     uint64_t ws, we;
     warp_subchunk(cs, ce, warp, ws, we);
     const uint64_t nsteps = (we - ws + kWdKeys - 1) / kWdKeys;
@@ -1218,7 +1221,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   {
     Scope sc(e, nm[2]);
     const int smem = kSampleChunk * (8 + 4 + 4);
-    k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms * 3), kLocalThreads, smem, e.stream>>>(
+    k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms), kSampleThreads, smem, e.stream>>>(
         st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
   }
   {

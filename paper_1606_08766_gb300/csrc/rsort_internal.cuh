@@ -22,7 +22,8 @@ constexpr int kMaxKDeep = 512;                    // buckets at levels >= 2
 constexpr int kBucketCap = 4096;                  // T_s: largest bucket one CTA sorts
 constexpr int kTargetBucket = 640;                // aim for this final bucket size
                                                   // (mostly below the 1024-key class)
-constexpr int kSampleChunk = 4096;                // sample sort: pairs per CTA chunk
+constexpr int kSampleChunk = 8192;                // sample sort: pairs per CTA chunk
+constexpr int kSampleThreads = 512;               // sample sort CTA
 constexpr int kDeepOversample = 16;               // samples per bucket at levels >= 2
 constexpr int kMaxLevels = 3;                     // partition levels before fallback
 constexpr int kLocalThreads = 256;                // in-SM bucket sort CTA
@@ -62,6 +63,8 @@ struct LevelSeg {
   uint32_t nchunks;
   uint32_t nschunks;
   uint32_t nunits;      // histogram units: nchunks (CTA chunks) or 8 * nchunks (warp sub-chunks)
+  uint32_t W;           // keys per chunk of this segment (all chunks equal but the last)
+  uint32_t pad;
 };
 
 // A bucket handed to the in-SM sort.
@@ -218,7 +221,17 @@ __device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint6
   const int cls = f.kind == kKindCopy ? kClassCopy
                   : f.kind == kKindBig ? kClassBig
                   : (f.size <= kSmallCap ? kClassSmall : kClassMedium);
-  const uint32_t slot = atomicAdd(&st->nfinal_c[cls], 1u);
+  // one atomic per (warp, class): the lanes appending to the same list share it
+  const uint32_t act = __activemask();
+  const uint32_t peers = __match_any_sync(act, (uint32_t)cls);
+  const int leader = __ffs(peers) - 1;
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&st->nfinal_c[cls], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  uint32_t lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  const uint32_t slot = base + __popc(peers & lt);
   if (slot < cap) items[(uint64_t)cls * cap + slot] = f;
   else atomicOr(&st->error, err_flag);
 }
