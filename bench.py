@@ -50,8 +50,6 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    # k_scatter, level 1 (k = 1024), n = 2^26: 1.301 GB read + 1.719 GB written
-    "L1.scatter": (1.301148e9 + 1.719255e9) / (1 << 26),
 }
 
 

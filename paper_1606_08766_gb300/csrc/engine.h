@@ -59,6 +59,9 @@ struct rsort_ctx {
   // tunable "warp_direct_max_k": warp-direct kernels up to this k (default off:
   // direct scattered stores measured ~3x slower than shared-memory combining)
   int wd_max_k = 0;
+  // tunable "wide_scatter_k": levels with at least this many buckets stage
+  // 4096-key sub-tiles with 512 threads (longer runs per bucket)
+  int wide_scatter_k = 1024;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

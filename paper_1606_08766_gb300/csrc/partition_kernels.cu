@@ -538,6 +538,32 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
   return s;
 }
 
+// Dynamic shared memory the wide (512-thread, 4096-key) scatter may use: the
+// device's opt-in limit minus the kernel's static shared memory, found when
+// the kernel attributes are set (0 until then, or if CUDA refused).  The wide
+// scatter runs only when its carve-up fits.
+static size_t g_wide_scatter_smem_max = 0;
+
+// Shared memory of the staged scatter with NW warps and ST-key sub-tiles.
+__host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, int nw, int st) {
+  size_t b = part_common_bytes(kmax, mode);
+  b += (size_t)(kmax + 1) * 4 + 4;
+  b += (size_t)nw * cnt_stride(kmax) * 2;
+  b = (b + 15) & ~(size_t)15;
+  return b + 2 * (size_t)st * (8 + 4 + 2);
+}
+
+__device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int mode, int nw) {
+  PartSmem s = carve(base, kmax, false, mode);
+  unsigned char* p = base + part_common_bytes(kmax, mode);
+  s.sbase = (uint32_t*)p;
+  p += (size_t)(kmax + 1) * 4 + 4;
+  s.wcnt = (uint16_t*)p;
+  p += (size_t)nw * cnt_stride(kmax) * 2;
+  s.buf = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  return s;
+}
+
 // Steps 4 + 5a: classify every element and count, per chunk of W elements,
 // how many fall into each bucket.  hist is laid out per segment bucket-major:
 // hist[hist_off + b * nchunks + chunk].  The chunk's keys stream through a
@@ -681,13 +707,18 @@ k_scan_down(const DevState* st, uint32_t* a, const uint32_t* sums) {
 // then counting-sorted by bucket into its own buffer and every bucket's run is
 // written out contiguously (write-combining through shared memory), so
 // buckets keep input order.
-__global__ void __launch_bounds__(kPartThreads, 2)
+template <int NT, int ST>
+__global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1))
 k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
           const uint32_t* ssi, const uint32_t* hist_scan, Dst dst, uint32_t W, uint32_t kmax,
           int unmap_out, int mode) {
+  constexpr int NW = NT / 32;
+  constexpr int IT = ST / NT;
+  static_assert(IT * 32 * NW == ST, "warp w owns IT*32 consecutive keys of a sub-tile");
+  constexpr size_t BUFB = (size_t)ST * (8 + 4 + 2);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PartSmem sm = carve(smem_raw, kmax, true, mode);
-  __shared__ uint64_t scan_sm[kPartWarps];
+  PartSmem sm = carve_scatter(smem_raw, kmax, mode, NW);
+  __shared__ uint64_t scan_sm[NW];
   // sub-tile buffer i: keys, positions, bucket ids (addressed arithmetically so
   // that no descriptor array lives in local memory)
   struct Buf {
@@ -696,11 +727,11 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
     uint16_t* b;
   };
   auto buf_of = [&](uint64_t i) {
-    unsigned char* p = sm.buf + (size_t)(i & 1) * kSBufBytes;
+    unsigned char* p = sm.buf + (size_t)(i & 1) * BUFB;
     Buf r;
     r.key = (uint64_t*)p;
-    r.idx = (uint32_t*)(p + (size_t)kST * 8);
-    r.b = (uint16_t*)(p + (size_t)kST * 12);
+    r.idx = (uint32_t*)(p + (size_t)ST * 8);
+    r.b = (uint16_t*)(p + (size_t)ST * 12);
     return r;
   };
   const uint64_t pol = l2_evict_first_policy();
@@ -717,22 +748,22 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
     const LevelSeg sg = segs[g];
     __syncthreads();
     if (g != cur_g) {
-      load_splitters<kPartThreads>(sg, ssk, ssi, sm.sp);
+      load_splitters<NT>(sg, ssk, ssi, sm.sp);
       cur_g = g;
     }
     const uint32_t k = sg.k;
     const uint64_t cl = c - sg.chunk_off;
-    for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
+    for (uint32_t b = threadIdx.x; b < k; b += NT)
       sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] + sg.delta);
     const uint64_t cs = sg.start + cl * sg.W;
     const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
-    const uint64_t nst = (ce - cs + kST - 1) / kST;
+    const uint64_t nst = (ce - cs + ST - 1) / ST;
     auto issue = [&](uint64_t s) {
       if (s < nst) {
-        const uint64_t b0 = cs + s * kST;
-        const uint32_t len = (uint32_t)umin64(kST, ce - b0);
+        const uint64_t b0 = cs + s * ST;
+        const uint32_t len = (uint32_t)umin64(ST, ce - b0);
         const Buf B = buf_of(s);
-        for (uint32_t t = threadIdx.x; t < len; t += kPartThreads) {
+        for (uint32_t t = threadIdx.x; t < len; t += NT) {
           cp_async_8(B.key + t, src.key + b0 + t, pol);
           if (src.idx) cp_async_4(B.idx + t, src.idx + b0 + t, pol);
         }
@@ -745,26 +776,26 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       __syncthreads();
       issue(s + 1);
       const Buf B = buf_of(s);
-      const uint64_t b0 = cs + s * kST;
-      const uint32_t len = (uint32_t)umin64(kST, ce - b0);
-      const uint32_t q0 = (uint32_t)warp * (kSItems * 32) + lane;
-      uint64_t key[kSItems];
-      uint32_t idx[kSItems];
-      uint32_t bk[kSItems];
-      uint32_t lrank[kSItems];
+      const uint64_t b0 = cs + s * ST;
+      const uint32_t len = (uint32_t)umin64(ST, ce - b0);
+      const uint32_t q0 = (uint32_t)warp * (IT * 32) + lane;
+      uint64_t key[IT];
+      uint32_t idx[IT];
+      uint32_t bk[IT];
+      uint32_t lrank[IT];
 #pragma unroll
-      for (int r = 0; r < kSItems; ++r) {
+      for (int r = 0; r < IT; ++r) {
         const uint32_t q = q0 + r * 32;
         const bool v = q < len;
         const uint64_t kv = v ? B.key[q] : 0;
         key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
         idx[r] = v ? (src.idx ? B.idx[q] : (uint32_t)(b0 + q - sg.start)) : 0;
       }
-      classify_batch<kSItems>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
+      classify_batch<IT>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
 #pragma unroll
-      for (int r = 0; r < kSItems; ++r) {
+      for (int r = 0; r < IT; ++r) {
         const bool v = q0 + r * 32 < len;
         const uint32_t b = v ? bk[r] : 0xffffffffu;
         bk[r] = b;
@@ -777,10 +808,10 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       }
       __syncthreads();
       // per bucket: exclusive prefix over warps (in place) and the sub-tile total
-      for (uint32_t b = threadIdx.x; b < k; b += kPartThreads) {
+      for (uint32_t b = threadIdx.x; b < k; b += NT) {
         uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < kPartWarps; ++w) {
+        for (int w = 0; w < NW; ++w) {
           const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
           sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
           tot += cnt;
@@ -789,13 +820,13 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       }
       __syncthreads();
       {  // exclusive scan of the k sub-tile totals (one thread per run of buckets)
-        const uint32_t per = (k + kPartThreads - 1) / kPartThreads;
+        const uint32_t per = (k + NT - 1) / NT;
         const uint32_t bb0 = threadIdx.x * per;
         const uint32_t bb1 = bb0 + per < k ? bb0 + per : k;
         uint32_t loc = 0;
         for (uint32_t b = bb0; b < bb1; ++b) loc += sm.sbase[b];
         uint64_t tot;
-        uint32_t run = (uint32_t)block_excl_scan_u64<kPartThreads>(loc, &tot, scan_sm);
+        uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
         for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t t = sm.sbase[b];
           sm.sbase[b] = run;
@@ -806,7 +837,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       __syncthreads();
       // counting-sort the sub-tile by bucket into its own buffer
 #pragma unroll
-      for (int r = 0; r < kSItems; ++r) {
+      for (int r = 0; r < IT; ++r) {
         const uint32_t b = bk[r];
         if (b != 0xffffffffu) {
           const uint32_t q = sm.sbase[b] + my_cnt[b] + lrank[r];
@@ -816,7 +847,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         }
       }
       __syncthreads();
-      for (uint32_t q = threadIdx.x; q < len; q += kPartThreads) {
+      for (uint32_t q = threadIdx.x; q < len; q += NT) {
         const uint32_t b = B.b[q];
         const uint64_t d = (uint64_t)sm.hist[b] + (q - sm.sbase[b]);
         const uint64_t kv = B.key[q];
@@ -824,7 +855,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         st_keep_u32(dst.idx + d, B.idx[q], pol_keep);
       }
       __syncthreads();
-      for (uint32_t b = threadIdx.x; b < k; b += kPartThreads)
+      for (uint32_t b = threadIdx.x; b < k; b += NT)
         sm.hist[b] += sm.sbase[b + 1] - sm.sbase[b];
     }
     cp_async_wait<0>();
@@ -1117,7 +1148,26 @@ void set_partition_kernel_attributes() {
   const size_t c = umax64(part_smem_bytes(kMaxK, false, 0), part_smem_bytes(kMaxK, false, 1));
   const size_t s = umax64(part_smem_bytes(kMaxK, true, 0), part_smem_bytes(kMaxK, true, 1));
   cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
-  cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s);
+  (void)s;
+  cudaFuncSetAttribute(k_scatter<kPartThreads, 2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)umax64(scatter_smem_bytes(kMaxK, 0, kPartWarps, 2048),
+                                   scatter_smem_bytes(kMaxK, 1, kPartWarps, 2048)));
+  {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    size_t limit = 0;
+    if (cudaFuncGetAttributes(&fa, k_scatter<512, 4096>) == cudaSuccess &&
+        (size_t)optin > fa.sharedSizeBytes) {
+      limit = (size_t)optin - fa.sharedSizeBytes;
+      if (cudaFuncSetAttribute(k_scatter<512, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)limit) != cudaSuccess)
+        limit = 0;
+    }
+    g_wide_scatter_smem_max = limit;
+  }
+  cudaGetLastError();  // a refused attribute only disables the variant
   const size_t w = umax64(wd_smem_bytes(kMaxK, 0), wd_smem_bytes(kMaxK, 1));
   cudaFuncSetAttribute(k_classify_count_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w);
   cudaFuncSetAttribute(k_scatter_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w);
@@ -1138,9 +1188,18 @@ int part_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
   int nb = 0;
   const size_t smem = part_smem_bytes(kmax, scatter, mode);
   if (scatter)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter, kPartThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<kPartThreads, 2048>,
+                                                  kPartThreads,
+                                                  scatter_smem_bytes(kmax, mode, kPartWarps, 2048));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count, kPartThreads, smem);
+  return nb > 0 ? nb : 1;
+}
+
+int wide_scatter_blocks_per_sm(uint32_t kmax, int mode) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<512, 4096>, 512,
+                                                scatter_smem_bytes(kmax, mode, 16, 4096));
   return nb > 0 ? nb : 1;
 }
 
@@ -1269,10 +1328,18 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       k_scatter_wd<<<grid_wd_s, kPartThreads, smem_wd, e.stream>>>(
           st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
           mode);
+    else if (kmax_level >= P.wide_scatter_k &&
+             scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096) <= g_wide_scatter_smem_max)
+      k_scatter<512, 4096><<<grid_for(P.chunk_cap, 1,
+                                      sms * wide_scatter_blocks_per_sm((uint32_t)kmax_level, mode)),
+                             512, scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096),
+                             e.stream>>>(st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W,
+                                         (uint32_t)kmax_level, unmap_out, mode);
     else
-      k_scatter<<<grid_s, kPartThreads, smem_s, e.stream>>>(
-          st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
-          mode);
+      k_scatter<kPartThreads, 2048>
+          <<<grid_s, kPartThreads, scatter_smem_bytes((uint32_t)kmax_level, mode, kPartWarps, 2048),
+             e.stream>>>(st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W,
+                         (uint32_t)kmax_level, unmap_out, mode);
   }
   {
     Scope sc(e, nm[9]);

@@ -104,6 +104,7 @@ struct Plan {
   bool need_tmp = false;
   int classifier = 0;       // 0: splitter tree, 1: leading-bits table
   int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
+  int wide_scatter_k = 1024;  // levels with at least this many buckets use wide sub-tiles
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
@@ -203,6 +204,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level
   P.level1_oversample = 1;
   P.classifier = p.classifier;
   P.warp_direct = kmax_level <= p.wd_max_k ? 1 : 0;
+  P.wide_scatter_k = p.wide_scatter_k;
   return P;
 }
 
@@ -273,6 +275,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   if (strcmp(name, "warp_direct_max_k") == 0) {
     if (v < 0 || v > kMaxK) return RSORT_EINVAL;
     c->wd_max_k = (int)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "wide_scatter_k") == 0) {
+    if (v < 1) return RSORT_EINVAL;
+    c->wide_scatter_k = (int)v;
     return RSORT_OK;
   }
   if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
@@ -347,6 +354,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
   Plan p;
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
+  p.wide_scatter_k = c->wide_scatter_k;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (n <= (uint64_t)kBucketCap) {
     p.n = n;
@@ -367,6 +375,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   Plan p;
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
+  p.wide_scatter_k = c->wide_scatter_k;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
   p.final_cap += num_segments;
@@ -552,6 +561,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   Plan p;
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
+  p.wide_scatter_k = c->wide_scatter_k;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -707,6 +717,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "serve_slots") == 0) {
     *value = c->serve_slots;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "wide_scatter_k") == 0) {
+    *value = c->wide_scatter_k;
     return RSORT_OK;
   }
   if (strcmp(name, "serve_batch_keys") == 0) {

@@ -114,6 +114,7 @@ struct LevelParams {
   int level1_oversample;  // 1: a = 16 ceil(log2 k) for hinted k (the paper's rule)
   int classifier;         // 0: splitter tree, 1: leading-bits table
   int warp_direct;        // 1: per-warp sub-chunks scattered straight to HBM
+  int wide_scatter_k;     // levels with at least this many buckets scatter 4096-key sub-tiles
 };
 
 // Element source / destination of a level.

@@ -194,6 +194,7 @@ CONFIGS = {
     "tree_staged": {"classifier": 0, "warp_direct_max_k": 0},
     "tree_warpdirect": {"classifier": 0, "warp_direct_max_k": 2048},
     "table_warpdirect": {"classifier": 1, "warp_direct_max_k": 2048},
+    "wide_scatter_everywhere": {"classifier": 1, "wide_scatter_k": 2},
 }
 
 
