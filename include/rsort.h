@@ -240,6 +240,11 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                the bin.
  *   serve_slots, serve_batch_keys, serve_alone_min  serving runtime (see
  *                rsort_submit); fixed once the runtime has started.
+ *   target_bucket  automatic fan-outs aim at final buckets of this many keys
+ *                (64..4096, default 640).
+ *   wide_scatter_k  levels with at least this many buckets stage 4096-key
+ *                sub-tiles with 512 threads when shared memory allows
+ *                (default 1024).
  *   warp_direct_max_k  partition levels with at most this many buckets per
  *                segment classify and scatter per warp sub-chunk straight to
  *                HBM; larger levels stage every sub-tile through shared

@@ -62,6 +62,9 @@ struct rsort_ctx {
   // tunable "wide_scatter_k": levels with at least this many buckets stage
   // 4096-key sub-tiles with 512 threads (longer runs per bucket)
   int wide_scatter_k = 1024;
+  // tunable "target_bucket": automatic fan-outs aim at final buckets of this
+  // many keys (mostly below the 1024-key in-SM size class)
+  uint32_t target_bucket = rsort::kTargetBucket;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

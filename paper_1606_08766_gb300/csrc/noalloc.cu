@@ -118,6 +118,7 @@ extern "C" rsort_status rsort_partition_noalloc(rsort_key_type type, const void*
   P.classifier = 0;
   P.warp_direct = 0;
   P.wide_scatter_k = 1 << 30;  // always the 2048-key sub-tile scatter
+  P.target_bucket = kTargetBucket;
 
   uint64_t o = 0;
   auto take = [&](uint64_t bytes) {

@@ -298,7 +298,7 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       if (in.k_hint >= 1) {
         k = min(in.k_hint, kmax_level);
       } else {
-        const uint64_t want = ((uint64_t)in.m + kTargetBucket - 1) / kTargetBucket;
+        const uint64_t want = ((uint64_t)in.m + P.target_bucket - 1) / P.target_bucket;
         k = (uint32_t)umax64(2, umin64(want, kmax_level));
       }
       const uint64_t a = (in.k_hint >= 1 && P.level1_oversample)

@@ -105,6 +105,7 @@ struct Plan {
   int classifier = 0;       // 0: splitter tree, 1: leading-bits table
   int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
   int wide_scatter_k = 1024;  // levels with at least this many buckets use wide sub-tiles
+  uint32_t target_bucket = kTargetBucket;  // automatic fan-out target
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
@@ -158,7 +159,7 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   p.seg_cap = std::max<uint64_t>(g1, segs_deep);
   const uint32_t kmax1 = k1 >= 2 ? k1 : kMaxKDeep;
   // level 1
-  p.bucket_cap1 = k1 >= 2 ? (uint64_t)k1 * g1 : n / kTargetBucket + g1 + 1;
+  p.bucket_cap1 = k1 >= 2 ? (uint64_t)k1 * g1 : n / p.target_bucket + g1 + 1;
   p.bucket_cap1 = std::min<uint64_t>(p.bucket_cap1, (uint64_t)kmax1 * g1);
   const uint64_t a1 = k1 >= 2 ? 16ull * ceil_log2_host(k1) : (uint64_t)kDeepOversample;
   p.samp_cap1 = std::min<uint64_t>(n, a1 * p.bucket_cap1);
@@ -167,7 +168,7 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   p.hist_cap1 = ((uint64_t)kmax1 * (n / p.W1) + p.bucket_cap1) * kPartWarps;
   p.schunk_cap1 = p.samp_cap1 / kSampleChunk + g1 + 1;
   // deeper levels
-  const uint64_t bucket_capd = n / kTargetBucket + segs_deep + 1;
+  const uint64_t bucket_capd = n / p.target_bucket + segs_deep + 1;
   const uint64_t samp_capd = std::min<uint64_t>(n, (uint64_t)kDeepOversample * bucket_capd);
   const uint64_t chunk_capd = n / p.Wd + segs_deep + 1;
   const uint64_t hist_capd = ((uint64_t)kMaxKDeep * (n / p.Wd) + bucket_capd) * kPartWarps;
@@ -205,6 +206,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level
   P.classifier = p.classifier;
   P.warp_direct = kmax_level <= p.wd_max_k ? 1 : 0;
   P.wide_scatter_k = p.wide_scatter_k;
+  P.target_bucket = p.target_bucket;
   return P;
 }
 
@@ -282,6 +284,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->wide_scatter_k = (int)v;
     return RSORT_OK;
   }
+  if (strcmp(name, "target_bucket") == 0) {
+    if (v < 64 || v > kBucketCap) return RSORT_EINVAL;
+    c->target_bucket = (uint32_t)v;
+    return RSORT_OK;
+  }
   if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
   if (strcmp(name, "serve_slots") == 0) {
     if (v < 1 || v > 8) return RSORT_EINVAL;
@@ -355,6 +362,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
+  p.target_bucket = c->target_bucket;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (n <= (uint64_t)kBucketCap) {
     p.n = n;
@@ -376,6 +384,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
+  p.target_bucket = c->target_bucket;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
   p.final_cap += num_segments;
@@ -562,6 +571,7 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   p.classifier = c->classifier;
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
+  p.target_bucket = c->target_bucket;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -721,6 +731,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "wide_scatter_k") == 0) {
     *value = c->wide_scatter_k;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "target_bucket") == 0) {
+    *value = c->target_bucket;
     return RSORT_OK;
   }
   if (strcmp(name, "serve_batch_keys") == 0) {

@@ -115,6 +115,7 @@ struct LevelParams {
   int classifier;         // 0: splitter tree, 1: leading-bits table
   int warp_direct;        // 1: per-warp sub-chunks scattered straight to HBM
   int wide_scatter_k;     // levels with at least this many buckets scatter 4096-key sub-tiles
+  uint32_t target_bucket; // automatic fan-out aims at buckets of this many keys
 };
 
 // Element source / destination of a level.
