@@ -479,6 +479,7 @@ struct PartSmem {
   uint32_t* hist;      // [K]   classify: counts;  scatter: running offsets
   uint32_t* sbase;     // [K+1] scatter: sub-tile bucket starts
   uint16_t* wcnt;      // [kPartWarps][cnt_stride(K)] scatter: per-warp counts / bases
+  uint8_t* wwin;       // [kPartWarps][K] scatter: per-warp winner lane of each bucket
   unsigned char* buf;  // classify: kCStages key stages; scatter: two sub-tile buffers
 };
 
@@ -529,6 +530,7 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
   p = base + part_common_bytes(kmax, mode);
   s.sbase = nullptr;
   s.wcnt = nullptr;
+  s.wwin = nullptr;
   if (scatter) {
     s.sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4 + 4;
     s.wcnt = (uint16_t*)p; p += (size_t)kPartWarps * cnt_stride(kmax) * 2;
@@ -549,6 +551,7 @@ __host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, in
   size_t b = part_common_bytes(kmax, mode);
   b += (size_t)(kmax + 1) * 4 + 4;
   b += (size_t)nw * cnt_stride(kmax) * 2;
+  b += (size_t)nw * kmax;
   b = (b + 15) & ~(size_t)15;
   return b + 2 * (size_t)st * (8 + 4 + 2);
 }
@@ -560,6 +563,8 @@ __device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int
   p += (size_t)(kmax + 1) * 4 + 4;
   s.wcnt = (uint16_t*)p;
   p += (size_t)nw * cnt_stride(kmax) * 2;
+  s.wwin = (uint8_t*)p;
+  p += (size_t)nw * kmax;
   s.buf = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
   return s;
 }
@@ -742,6 +747,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
   const uint32_t ltmask = lanemask_lt();
   const uint32_t kst = cnt_stride(kmax);
   uint16_t* my_cnt = sm.wcnt + (size_t)warp * kst;
+  uint8_t* my_win = sm.wwin + (size_t)warp * kmax;
   uint32_t cur_g = 0xffffffffu;
   for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
     const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
@@ -752,6 +758,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       cur_g = g;
     }
     const uint32_t k = sg.k;
+    const int nbits = k > 32 ? 5 : (int)ceil_log2_dev(k);
     const uint64_t cl = c - sg.chunk_off;
     for (uint32_t b = threadIdx.x; b < k; b += NT)
       sm.hist[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] + sg.delta);
@@ -799,7 +806,27 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         const bool v = q0 + r * 32 < len;
         const uint32_t b = v ? bk[r] : 0xffffffffu;
         bk[r] = b;
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        // peers = the lanes holding the same bucket.  Up to 32 buckets the
+        // bucket bits are compared by ballots; beyond, every lane first writes
+        // its lane id to the warp's slot of its bucket, and the lane id that
+        // stayed there (one per distinct bucket) is compared instead: 5
+        // ballots whatever k is.
+        uint32_t w = b;
+        if (k > 32) {
+          if (v) my_win[b] = (uint8_t)lane;
+          __syncwarp();
+          w = v ? my_win[b] : 0u;
+          __syncwarp();
+        }
+        uint32_t peers = __ballot_sync(0xffffffffu, v);
+#pragma unroll
+        for (int bit = 0; bit < 5; ++bit) {
+          if (bit < nbits) {
+            const bool one = (w >> bit) & 1u;
+            const uint32_t m = __ballot_sync(0xffffffffu, one);
+            peers &= one ? m : ~m;
+          }
+        }
         const uint32_t c0 = v ? my_cnt[b] : 0;
         __syncwarp();
         if (v && lane == __ffs(peers) - 1) my_cnt[b] = (uint16_t)(c0 + __popc(peers));
