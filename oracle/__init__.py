@@ -62,6 +62,10 @@ def _load():
                                              ctypes.c_uint32, ctypes.c_uint64, u64p, u64p,
                                              u32p, u32p, u64p, u32p, u64p]
             lib.oracle_partition.restype = ctypes.c_int
+            lib.oracle_partition_ex.argtypes = [u64p, ctypes.c_uint64, ctypes.c_int,
+                                                ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                                ctypes.c_uint32, u64p, u32p, u64p, u32p, u64p]
+            lib.oracle_partition_ex.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -144,5 +148,35 @@ def partition(keys, k: int, seed: int, key_type: int = KEY_U64):
     out["spl_key"] = out["spl_key"][:max(k - 1, 0)]
     out["spl_pos"] = out["spl_pos"][:max(k - 1, 0)]
     for name in ("bucket", "keys_out", "pos_out"):
+        out[name] = out[name][:n]
+    return out
+
+
+def partition_ex(keys, k: int, seed: int, key_type: int = KEY_U64, tie_break: bool = True,
+                 over: int = 1):
+    """The partition step with the NTB switch (tie_break=False: classify by key
+    only) and AMS overpartitioning (over = b > 1: b*k fine partitions grouped
+    greedily into k outputs).
+
+    Returns a dict with fine_sizes [b*k], group_first [k+1], keys_out, pos_out
+    and offsets [k+1]."""
+    kb = _as_bits(keys)
+    n = kb.shape[0]
+    K = k * over
+    out = {
+        "fine_sizes": np.empty(max(K, 1), np.uint64),
+        "group_first": np.empty(k + 1, np.uint32),
+        "keys_out": np.empty(max(n, 1), np.uint64),
+        "pos_out": np.empty(max(n, 1), np.uint32),
+        "offsets": np.empty(k + 1, np.uint64),
+    }
+    rc = _load().oracle_partition_ex(_p64(kb), n, key_type, k, seed & (2**64 - 1),
+                                     1 if tie_break else 0, over, _p64(out["fine_sizes"]),
+                                     _p32(out["group_first"]), _p64(out["keys_out"]),
+                                     _p32(out["pos_out"]), _p64(out["offsets"]))
+    if rc:
+        raise ValueError("oracle_partition_ex rejected its arguments")
+    out["fine_sizes"] = out["fine_sizes"][:K]
+    for name in ("keys_out", "pos_out"):
         out[name] = out[name][:n]
     return out

@@ -30,6 +30,14 @@
  *                      lexicographically smaller than (key, position), and lay
  *                      the partitions out in order.
  *
+ *   oracle_partition_ex  The same step with the two switches the paper
+ *                      measures around it: classification by key only (the
+ *                      NTB ablation of Section 6) and AMS-sort
+ *                      overpartitioning (b*k fine partitions assigned to the
+ *                      k outputs by a greedy scan that minimises the largest
+ *                      output; Section 3 "AMS-sort", Appendix "Implementation
+ *                      Details").
+ *
  * Readings where the paper is silent (each also listed in the design doc):
  *   - phi: 64-bit floating-point elements (Appendix "Experimental Results") are
  *     ordered by their IEEE-754 bit pattern mapped to an unsigned integer
@@ -43,6 +51,14 @@
  *     size), with h the splitmix64 generator
  *     (Steele, Lea & Flood 2014): h(s, j) = mix(s + (j+1) * 0x9e3779b97f4a7c15).
  *   - splitter j (j = 1..k-1) is the sorted sample's element floor(j*S/k).
+ *   - NTB: an element equal to a splitter key goes below it (the search counts
+ *     splitter keys strictly smaller than x, as the Super Scalar Sample Sort
+ *     descent does).
+ *   - overpartitioning: the sample is the plain step's (the paper sorts
+ *     O(k log k) samples per level whatever b is); fine splitter j
+ *     (j = 1..b*k-1) is sorted sample floor(j*S/(b*k)); "a greedy algorithm
+ *     ... minimizing the load imbalance" is read as: the smallest bound L for
+ *     which the in-order greedy scan needs at most k groups, then that scan.
  *
  * parity pins: see tests/test_oracle_pins.py.  All functions are pinned.
  */
@@ -290,6 +306,183 @@ done:
     free(sscr);
     free(tk);
     free(ti);
+    free(cnt);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Partition-step variants: NTB ablation and AMS overpartitioning           */
+/* ---------------------------------------------------------------------- */
+
+/* Greedy assignment of consecutive fine partitions (sizes c[0..K)) to groups
+ * under a load bound L >= max c: the fine partitions are visited in order and
+ * a new group is opened whenever adding the next one would lift the current
+ * group above L.  Returns the number of groups used; if first != NULL (room
+ * for kmax entries) first[g] receives the fine partition group g starts at. */
+static uint64_t greedy_groups(const uint64_t *c, uint32_t K, uint64_t L, uint32_t *first,
+                              uint32_t kmax)
+{
+    uint64_t groups = 1, load = 0;
+    if (first && kmax > 0)
+        first[0] = 0;
+    for (uint32_t j = 0; j < K; ++j) {
+        if (load + c[j] > L) {
+            if (first && groups < kmax)
+                first[groups] = j;
+            ++groups;
+            load = 0;
+        }
+        load += c[j];
+    }
+    return groups;
+}
+
+/* The partition step with the two switches the paper evaluates around it.
+ *
+ *   tie_break = 1  the robust classification of oracle_partition:
+ *                  fine partition of (x, i) = #{ splitters lexicographically
+ *                  smaller than (x, i) }.
+ *   tie_break = 0  the "no tie-breaking" ablation (NTB-AMS, Section 6,
+ *                  figure "RAMS vs NTB-AMS"): the same splitters, but the
+ *                  classification looks at keys only,
+ *                  #{ splitters whose key is smaller than x }, so every copy
+ *                  of a key lands in one partition.
+ *   over = b >= 1  AMS-sort overpartitioning (Section 3, AMS-sort; Appendix
+ *                  "Implementation Details": b = 2 / ((1 + eps)^(1/l) - 1)):
+ *                  the same sample yields K = b*k partitions (splitter j,
+ *                  j = 1..K-1, is sorted sample floor(j*S/K)); their exact
+ *                  sizes are counted and consecutive fine partitions are
+ *                  assigned to the k outputs by the greedy scan above, with
+ *                  the smallest bound L for which k groups suffice, which
+ *                  minimises the largest output.  b = 1 is the plain step
+ *                  (no grouping: output g is partition g).
+ *
+ * The sample is the one of oracle_partition (S = oracle_sample_count(n, k),
+ * stratified, sorted by (key, position)).  Outputs (NULL to skip):
+ *   fine_sizes  [b*k]  exact size of every fine partition
+ *   group_first [k+1]  first fine partition of every output; K past the end
+ *   keys_out, pos_out [n], offsets [k+1]  as in oracle_partition.
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_partition_ex(const uint64_t *keys_bits, uint64_t n, int key_type, uint32_t k,
+                        uint64_t seed, int tie_break, uint32_t over, uint64_t *fine_sizes,
+                        uint32_t *group_first, uint64_t *keys_out, uint32_t *pos_out,
+                        uint64_t *offsets)
+{
+    if (k == 0 || over == 0 || n > 0xFFFFFFFFULL || (key_type != 0 && key_type != 1) ||
+        (uint64_t)k * over > 0xFFFFFFFFULL)
+        return -1;
+    const uint32_t K = k * over;
+    uint64_t S = oracle_sample_count(n, k);
+    uint64_t *key = (uint64_t *)malloc((n ? n : 1) * sizeof(uint64_t));
+    uint32_t *fb = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    uint32_t *grp = (uint32_t *)malloc((n ? n : 1) * sizeof(uint32_t));
+    uint32_t *order = (uint32_t *)malloc((S ? S : 1) * sizeof(uint32_t));
+    uint32_t *sscr = (uint32_t *)malloc((S ? S : 1) * sizeof(uint32_t));
+    uint64_t *tk = (uint64_t *)malloc((size_t)K * sizeof(uint64_t));
+    uint32_t *ti = (uint32_t *)malloc((size_t)K * sizeof(uint32_t));
+    uint64_t *c = (uint64_t *)calloc((size_t)K, sizeof(uint64_t));
+    uint32_t *first = (uint32_t *)malloc(((size_t)k + 1) * sizeof(uint32_t));
+    uint64_t *cnt = (uint64_t *)calloc((size_t)k + 1, sizeof(uint64_t));
+    int rc = -1;
+    if (!key || !fb || !grp || !order || !sscr || !tk || !ti || !c || !first || !cnt)
+        goto done;
+    for (uint64_t i = 0; i < n; ++i)
+        key[i] = phi(keys_bits[i], key_type);
+
+    /* sample and rank it exactly as oracle_partition does */
+    for (uint64_t j = 0; j < S; ++j) {
+        uint64_t lo = (j * n) / S, hi = ((j + 1) * n) / S;
+        order[j] = (uint32_t)(lo + oracle_splitmix64_at(seed, j) % (hi - lo));
+    }
+    merge_sort(order, sscr, 0, S, key);
+
+    /* K - 1 fine splitters: every S/K-th sample */
+    for (uint32_t j = 1; j < K && S > 0; ++j) {
+        uint64_t r = ((uint64_t)j * S) / K;
+        tk[j - 1] = key[order[r]];
+        ti[j - 1] = order[r];
+    }
+
+    /* fine classification, with or without positions as tie-breakers */
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t f = 0;
+        for (uint32_t j = 0; j + 1 < K; ++j) {
+            int smaller = tie_break ? pair_less(tk[j], ti[j], key[i], i) : (tk[j] < key[i]);
+            if (smaller)
+                ++f;
+        }
+        fb[i] = f;
+        c[f] += 1;
+    }
+
+    /* groups: the smallest bound L with at most k greedy groups.  Every group
+     * holds at least ceil(n/k) elements in the worst case and at least the
+     * largest fine partition; the bound ceil(n/k) + max c always suffices
+     * (each closed group then exceeds n/k, so k of them would exceed n). */
+    uint64_t maxc = 0;
+    for (uint32_t j = 0; j < K; ++j)
+        if (c[j] > maxc)
+            maxc = c[j];
+    uint64_t lo = (n + k - 1) / k;
+    if (maxc > lo)
+        lo = maxc;
+    uint64_t hi = (n + k - 1) / k + maxc;
+    if (hi < lo)
+        hi = lo;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (greedy_groups(c, K, mid, NULL, 0) <= k)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    for (uint32_t g = 0; g <= k; ++g)
+        first[g] = K;
+    if (over == 1) {
+        /* no overpartitioning: output g is fine partition g */
+        for (uint32_t g = 0; g < k; ++g)
+            first[g] = g;
+    } else {
+        greedy_groups(c, K, lo, first, k);
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t g = 0;
+        while (g + 1 < k && first[g + 1] <= fb[i])
+            ++g;
+        grp[i] = g;
+        cnt[g + 1] += 1;
+    }
+
+    /* lay the outputs out in order, each in increasing position */
+    for (uint32_t g = 0; g < k; ++g)
+        cnt[g + 1] += cnt[g];
+    if (offsets)
+        for (uint32_t g = 0; g <= k; ++g)
+            offsets[g] = cnt[g];
+    if (fine_sizes)
+        for (uint32_t j = 0; j < K; ++j)
+            fine_sizes[j] = c[j];
+    if (group_first)
+        for (uint32_t g = 0; g <= k; ++g)
+            group_first[g] = first[g];
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t o = cnt[grp[i]]++;
+        if (keys_out)
+            keys_out[o] = keys_bits[i];
+        if (pos_out)
+            pos_out[o] = (uint32_t)i;
+    }
+    rc = 0;
+done:
+    free(key);
+    free(fb);
+    free(grp);
+    free(order);
+    free(sscr);
+    free(tk);
+    free(ti);
+    free(c);
+    free(first);
     free(cnt);
     return rc;
 }
