@@ -396,8 +396,11 @@ int oracle_partition_ex(const uint64_t *keys_bits, uint64_t n, int key_type, uin
     }
     merge_sort(order, sscr, 0, S, key);
 
-    /* K - 1 fine splitters: every S/K-th sample */
-    for (uint32_t j = 1; j < K && S > 0; ++j) {
+    /* K - 1 fine splitters: every S/K-th sample.  Without a sample (S = 0,
+     * which the sample-size rule gives for k = 1) there are no splitters and
+     * every element is in fine partition 0. */
+    const uint32_t nfs = S > 0 ? K - 1 : 0;
+    for (uint32_t j = 1; j <= nfs; ++j) {
         uint64_t r = ((uint64_t)j * S) / K;
         tk[j - 1] = key[order[r]];
         ti[j - 1] = order[r];
@@ -406,7 +409,7 @@ int oracle_partition_ex(const uint64_t *keys_bits, uint64_t n, int key_type, uin
     /* fine classification, with or without positions as tie-breakers */
     for (uint64_t i = 0; i < n; ++i) {
         uint32_t f = 0;
-        for (uint32_t j = 0; j + 1 < K; ++j) {
+        for (uint32_t j = 0; j < nfs; ++j) {
             int smaller = tie_break ? pair_less(tk[j], ti[j], key[i], i) : (tk[j] < key[i]);
             if (smaller)
                 ++f;

@@ -184,3 +184,13 @@ def test_variant_edge_shapes(oracle_mod, n, k, over):
     res = oracle_mod.partition_ex(keys, k, seed=5, over=over)
     assert res["fine_sizes"].sum() == n
     _check_layout(oracle_mod, keys, res, k)
+
+
+def test_single_output_has_no_sample_and_one_fine_partition(oracle_mod):
+    # k = 1: the sample-size rule 16 * ceil(log2 k) * k draws no sample, so no
+    # fine splitter exists and everything is in fine partition 0
+    keys = instances.generate("uniform", 1000, p=4, seed=1)
+    res = oracle_mod.partition_ex(keys, 1, seed=2, over=7)
+    np.testing.assert_array_equal(res["fine_sizes"], np.array([1000, 0, 0, 0, 0, 0, 0], np.uint64))
+    np.testing.assert_array_equal(res["group_first"], np.array([0, 7], np.uint32))
+    np.testing.assert_array_equal(res["pos_out"], np.arange(1000, dtype=np.uint32))
