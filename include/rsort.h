@@ -102,6 +102,42 @@ rsort_status rsort_partition(rsort_ctx *ctx, rsort_key_type type, const void *d_
                              uint64_t n, uint32_t k, uint64_t seed, void *d_keys_out,
                              uint32_t *d_pos_out, uint64_t *d_offsets_out, void *stream);
 
+/* Options of rsort_partition_ex (NULL = the plain robust step). */
+typedef struct rsort_partition_opts {
+    /* 1: classify (key, position) pairs lexicographically -- the robust step;
+     * 0: classify by key only, #{splitter keys < x}, so all copies of a key
+     *    land in one partition: the "no tie-breaking" ablation the paper
+     *    measures against its robust AMS-sort (NTB-AMS, Section 6). */
+    uint32_t tie_break;
+    /* b >= 1.  b > 1: AMS-sort overpartitioning (Section 3 on AMS-sort;
+     * Appendix "Implementation Details" picks b = 2 / ((1+eps)^(1/l) - 1), so
+     * b = 10 for eps = 0.2 with one level).  The same sample gives b*k - 1
+     * fine splitters (sorted sample floor(j*S/(b*k)), j = 1..b*k-1); the exact
+     * sizes of the b*k fine partitions are counted, and consecutive fine
+     * partitions are assigned to the k outputs by an in-order greedy scan
+     * under the smallest load bound L that needs at most k groups (this
+     * minimises the largest output; L <= ceil(n/k) + largest fine partition).
+     * Requires b*k <= 10240.  b = 1: no overpartitioning. */
+    uint32_t overpartition;
+} rsort_partition_opts;
+
+/* rsort_partition with the options above.  Same arguments, layout and errors
+ * as rsort_partition, plus two optional device outputs (NULL to skip):
+ *   d_fine_sizes_out  [b*k] u64: size of every fine partition (b = 1: of
+ *                     every output);
+ *   d_group_first_out [k+1] u32: first fine partition of every output
+ *                     (output g holds fine partitions [first[g], first[g+1]);
+ *                     empty trailing outputs start at b*k).
+ * Output g holds, in increasing position, the elements whose fine partition
+ * lies in its range.  Errors: EINVAL (also tie_break > 1, overpartition == 0,
+ * b*k > 10240), ENOMEM, ECUDA. */
+rsort_status rsort_partition_ex(rsort_ctx *ctx, rsort_key_type type, const void *d_keys_in,
+                                uint64_t n, uint32_t k, uint64_t seed,
+                                const rsort_partition_opts *opts, void *d_keys_out,
+                                uint32_t *d_pos_out, uint64_t *d_offsets_out,
+                                uint64_t *d_fine_sizes_out, uint32_t *d_group_first_out,
+                                void *stream);
+
 /* Plain sort (Section 2's output contract): keys_out[j] = keys_in[perm[j]] with
  * (key, perm[j]) strictly increasing.  Large inputs run the multi-level robust
  * sample sort (level 1 with k = p_virtual buckets, deeper levels until buckets

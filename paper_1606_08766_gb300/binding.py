@@ -37,6 +37,10 @@ class _Stats(ctypes.Structure):
                 ("bytes_moved", ctypes.c_uint64), ("level_elems", ctypes.c_uint64 * 4)]
 
 
+class _PartOpts(ctypes.Structure):
+    _fields_ = [("tie_break", ctypes.c_uint32), ("overpartition", ctypes.c_uint32)]
+
+
 class _Request(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int32), ("d_keys_in", ctypes.c_void_p),
                 ("d_keys_out", ctypes.c_void_p), ("d_perm_out", ctypes.c_void_p),
@@ -88,6 +92,8 @@ def load_library(build_if_missing: bool = True):
         "rsort_strerror": (ctypes.c_char_p, [i32]),
         "rsort_check": (i32, [vp]),
         "rsort_partition": (i32, [vp, i32, vp, u64, u32, u64, vp, vp, vp, vp]),
+        "rsort_partition_ex": (i32, [vp, i32, vp, u64, u32, u64, ctypes.POINTER(_PartOpts),
+                                     vp, vp, vp, vp, vp, vp]),
         "rsort_sort": (i32, [vp, i32, vp, vp, vp, u64, u32, u64, vp, ctypes.POINTER(_Stats)]),
         "rsort_segmented": (i32, [vp, i32, vp, vp, vp, u64, vp, u32, u64, vp]),
         "rsort_partition_noalloc": (i32, [i32, vp, u64, u32, u64, vp, vp, vp, vp]),
@@ -249,6 +255,26 @@ class Context:
                                        _ptr(offsets), _stream_handle(stream))
         _check(rc, "rsort_partition")
         return keys_out, pos_out, offsets
+
+    def partition_ex(self, keys: torch.Tensor, k: int, seed: int = 1, tie_break: bool = True,
+                     overpartition: int = 1, key_type=None, stream=None):
+        """Partition step with the NTB switch and AMS overpartitioning:
+        (keys_out, positions, offsets[k+1], fine_sizes[b*k], group_first[k+1])."""
+        _check_keys(keys)
+        n = keys.numel()
+        dev = keys.device
+        keys_out = torch.empty_like(keys)
+        pos_out = torch.empty(n, dtype=torch.int32, device=dev)
+        offsets = torch.empty(k + 1, dtype=torch.int64, device=dev)
+        fine = torch.empty(max(k * overpartition, 1), dtype=torch.int64, device=dev)
+        first = torch.empty(k + 1, dtype=torch.int32, device=dev)
+        opts = _PartOpts(1 if tie_break else 0, overpartition)
+        rc = self._lib.rsort_partition_ex(self._ctx, _key_type(keys, key_type), _ptr(keys), n, k,
+                                          seed & (2**64 - 1), ctypes.byref(opts), _ptr(keys_out),
+                                          _ptr(pos_out), _ptr(offsets), _ptr(fine), _ptr(first),
+                                          _stream_handle(stream))
+        _check(rc, "rsort_partition_ex")
+        return keys_out, pos_out, offsets, fine[:k * overpartition], first
 
     def check(self):
         _check(self._lib.rsort_check(self._ctx), "rsort_check")

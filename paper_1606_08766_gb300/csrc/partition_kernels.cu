@@ -82,6 +82,7 @@ struct Splitters {
   int tbits;        // table bits
   int shift;        // key bits dropped before the table index
   int mode;         // 0 tree, 1 table
+  int ntb;          // 1: no tie-breaking, classify by key only (ablation)
   uint32_t nspl;    // k - 1
 };
 
@@ -177,7 +178,7 @@ __device__ __forceinline__ void classify_batch_tree(const uint64_t (&x)[R], uint
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     uint32_t bb = j[r] - (1u << sp.logK);
-    if (bb < sp.nspl && ub[r] == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
+    if (!sp.ntb && bb < sp.nspl && ub[r] == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
     b[r] = bb;
   }
 }
@@ -215,7 +216,7 @@ __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uin
         }
       }
       bb = lo;
-      if (bb < end && ub == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
+      if (!sp.ntb && bb < end && ub == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
     }
     b[r] = bb;
   }
@@ -490,9 +491,10 @@ __host__ __device__ inline uint32_t cnt_stride(uint32_t kmax) { return (kmax + 1
 // one scatter sub-tile buffer: keys, positions, bucket ids
 constexpr size_t kSBufBytes = (size_t)kST * (8 + 4 + 2);
 
+// mode: bit 0 the classifier (0 tree, 1 table), bit 1 no tie-breaking.
 __host__ __device__ inline size_t part_common_bytes(uint32_t kmax, int mode) {
   const size_t Kp = next_pow2_u32(kmax);
-  size_t b = mode == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
+  size_t b = (mode & 1) == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
   b += (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
   return (b + 15) & ~(size_t)15;
 }
@@ -514,10 +516,11 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
   PartSmem s;
   const size_t Kp = next_pow2_u32(kmax);
   unsigned char* p = base;
-  s.sp.mode = mode;
+  s.sp.mode = mode & 1;
+  s.sp.ntb = (mode >> 1) & 1;
   s.sp.tree = nullptr;
   s.sp.tbl = nullptr;
-  if (mode == 0) {
+  if (s.sp.mode == 0) {
     s.sp.tree = (uint64_t*)p;
     p += Kp * 8;
   } else {
@@ -1155,6 +1158,210 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
   }
 }
 
+// ---------------------------------------------------------------------------
+// AMS-sort overpartitioning of a one-segment step (Section 3, AMS-sort;
+// Appendix "Implementation Details": b = 2 / ((1 + eps)^(1/l) - 1)).
+//
+//   k_fine_count    exact sizes of the K = b*k fine partitions of the same
+//                   sample (fine splitter j = sorted sample floor(j*S/K)),
+//                   counted per CTA in shared memory
+//   k_group_greedy  one CTA: the smallest load bound L for which the in-order
+//                   greedy scan needs at most k groups (a 1024-way search per
+//                   round), then that scan; the k-1 group boundaries are
+//                   written after the sample as the splitters of the ordinary
+//                   k-way step, and the segment is pointed at them
+// ---------------------------------------------------------------------------
+constexpr int kFineThreads = 512;
+constexpr int kFineItems = 8;
+constexpr int kGreedyThreads = 1024;
+
+__host__ __device__ inline size_t fine_smem_bytes(uint32_t K) {
+  const uint32_t Kp = next_pow2_u32(K);
+  return ((size_t)4 << table_bits_for(Kp)) + (size_t)K * (8 + 4 + 4);
+}
+
+__host__ __device__ inline size_t greedy_smem_bytes(uint32_t K, uint32_t k) {
+  return (size_t)(K + 1) * 8 + (size_t)(k + 1) * 4;
+}
+
+__global__ void __launch_bounds__(kFineThreads, 1)
+k_fine_count(const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t* ssi,
+             uint32_t over, int ntb, uint32_t* fine_cnt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LevelSeg sg = segs[0];
+  const uint32_t K = sg.k * over;
+  // no sample (S = 0, the sample-size rule for k = 1): no fine splitters, so
+  // every element counts for fine partition 0
+  sg.k = sg.S > 0 ? K : 1;
+  Splitters sp;
+  sp.mode = 1;
+  sp.ntb = ntb;
+  sp.tree = nullptr;
+  unsigned char* p = smem_raw;
+  sp.tbl = (uint32_t*)p;
+  p += (size_t)4 << table_bits_for(next_pow2_u32(K));
+  sp.key = (uint64_t*)p;
+  p += (size_t)K * 8;
+  sp.idx = (uint32_t*)p;
+  p += (size_t)K * 4;
+  uint32_t* cnt = (uint32_t*)p;
+  load_splitters<kFineThreads>(sg, ssk, ssi, sp);
+  for (uint32_t b = threadIdx.x; b < K; b += kFineThreads) cnt[b] = 0;
+  __syncthreads();
+  constexpr uint64_t kSpan = (uint64_t)kFineThreads * kFineItems;
+  const uint64_t m = sg.m;
+  for (uint64_t base = (uint64_t)blockIdx.x * kSpan; base < m;
+       base += (uint64_t)gridDim.x * kSpan) {
+    uint64_t x[kFineItems];
+    uint32_t b[kFineItems];
+#pragma unroll
+    for (int r = 0; r < kFineItems; ++r) {
+      const uint64_t q = base + (uint64_t)r * kFineThreads + threadIdx.x;
+      x[r] = q < m ? load_key(src, sg.start + q) : 0;
+    }
+    // level 1 of a one-segment step: the position is the offset in the segment
+    classify_batch<kFineItems>(x, b, [&](int r) {
+      return (uint32_t)(base + (uint64_t)r * kFineThreads + threadIdx.x);
+    }, sp);
+#pragma unroll
+    for (int r = 0; r < kFineItems; ++r)
+      if (base + (uint64_t)r * kFineThreads + threadIdx.x < m) atomicAdd(&cnt[b[r]], 1u);
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < K; b += kFineThreads)
+    if (cnt[b]) atomicAdd(&fine_cnt[b], cnt[b]);
+}
+
+// End of the greedy group that starts at fine partition j0: the largest
+// j in (j0, K] with P[j] - P[j0] <= L (P: prefix sums, every size <= L).
+__device__ __forceinline__ uint32_t greedy_next(const uint64_t* P, uint32_t K, uint32_t j0,
+                                                uint64_t L) {
+  const uint64_t base = P[j0];
+  uint32_t lo = j0 + 1, step = 1;
+  while (lo + step <= K && P[lo + step] - base <= L) {
+    lo += step;
+    step *= 2;
+  }
+  uint32_t hi = lo + step <= K ? lo + step - 1 : K;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (P[mid] - base <= L) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Groups the greedy scan opens under bound L (stops counting past kmax).
+__device__ __forceinline__ uint32_t greedy_count(const uint64_t* P, uint32_t K, uint64_t L,
+                                                 uint32_t kmax) {
+  uint32_t g = 0, j = 0;
+  while (j < K && g <= kmax) {
+    j = greedy_next(P, K, j, L);
+    ++g;
+  }
+  return g == 0 ? 1 : g;
+}
+
+__global__ void __launch_bounds__(kGreedyThreads, 1)
+k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t scan_sm[kGreedyThreads / 32];
+  __shared__ uint32_t s_best;
+  const LevelSeg sg = segs[0];
+  const uint32_t k = sg.k, K = k * op.over;
+  uint64_t* P = (uint64_t*)smem_raw;                 // [K + 1]
+  uint32_t* first = (uint32_t*)(P + K + 1);          // [k + 1]
+  const uint32_t tid = threadIdx.x;
+  // prefix sums of the fine sizes, one run of fine partitions per thread
+  const uint32_t per = (K + kGreedyThreads - 1) / kGreedyThreads;
+  const uint32_t j0 = tid * per, j1 = j0 + per < K ? j0 + per : K;
+  uint64_t loc = 0, mx = 0;
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint64_t c = op.fine_cnt[j];
+    loc += c;
+    mx = c > mx ? c : mx;
+    if (op.fine_out) op.fine_out[j] = c;
+  }
+  uint64_t n;
+  uint64_t run = block_excl_scan_u64<kGreedyThreads>(loc, &n, scan_sm);
+  if (tid == 0) P[0] = 0;
+  for (uint32_t j = j0; j < j1; ++j) {
+    run += op.fine_cnt[j];
+    P[j + 1] = run;
+  }
+  // largest fine size (max-reduce through the scan scratch)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((tid & 31) == 0) scan_sm[tid >> 5] = mx;
+  __syncthreads();
+  uint64_t maxc = 0;
+  for (int w = 0; w < kGreedyThreads / 32; ++w) maxc = scan_sm[w] > maxc ? scan_sm[w] : maxc;
+  __syncthreads();
+  // bound: every group holds at least ceil(n/k) in the worst case and at least
+  // the largest fine partition; ceil(n/k) + maxc always needs at most k groups
+  const uint64_t avg = (n + k - 1) / k;
+  uint64_t lo = avg > maxc ? avg : maxc;
+  uint64_t hi = avg + maxc > lo ? avg + maxc : lo;
+  while (lo < hi) {
+    const uint64_t span = hi - lo;
+    const uint64_t L = lo + (span * (tid + 1)) / kGreedyThreads;
+    if (tid == 0) s_best = kGreedyThreads;
+    __syncthreads();
+    if (greedy_count(P, K, L, k) <= k) atomicMin(&s_best, tid);
+    __syncthreads();
+    const uint32_t t = s_best;  // t <= kGreedyThreads - 1: L(last) = hi is feasible
+    const uint64_t nhi = lo + (span * (t + 1)) / kGreedyThreads;
+    const uint64_t nlo = t == 0 ? lo : lo + (span * t) / kGreedyThreads + 1;
+    __syncthreads();
+    lo = nlo;
+    hi = nhi;
+  }
+  if (tid == 0) {
+    uint32_t g = 0, j = 0;
+    while (j < K && g < k) {
+      first[g++] = j;
+      j = greedy_next(P, K, j, lo);
+    }
+    if (g == 0) first[g++] = 0;
+    for (; g <= k; ++g) first[g] = K;
+  }
+  __syncthreads();
+  // group boundaries become the splitters of the k-way step, stored after the
+  // sample: entry g (g = 1..k-1) is fine splitter first[g] (an element-free
+  // sentinel above every pair when the group is empty and past the end)
+  const uint64_t extra = sg.samp_off + sg.S;
+  for (uint32_t g = tid + 1; g < k; g += kGreedyThreads) {
+    const uint32_t f = first[g];
+    uint64_t key = ~0ULL;
+    uint32_t idx = ~0u;
+    if (f < K) {
+      const uint64_t r = ((uint64_t)f * sg.S) / K;
+      key = ssk[sg.samp_off + r];
+      idx = ssi[sg.samp_off + r];
+    }
+    ssk[extra + g] = key;
+    ssi[extra + g] = idx;
+  }
+  if (op.first_out)
+    for (uint32_t g = tid; g <= k; g += kGreedyThreads) op.first_out[g] = first[g];
+  __syncthreads();
+  if (tid == 0) {
+    segs[0].samp_off = extra;
+    segs[0].S = k;
+  }
+}
+
+// Without overpartitioning the fine partitions are the outputs themselves.
+__global__ void k_plain_groups(const uint64_t* offsets, uint32_t k, uint64_t* fine_out,
+                               uint32_t* first_out) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= k; g += gridDim.x * blockDim.x) {
+    if (fine_out && g < k) fine_out[g] = offsets[g + 1] - offsets[g];
+    if (first_out) first_out[g] = g;
+  }
+}
+
 inline int grid_for(uint64_t work, int per_block, int max_blocks) {
   uint64_t b = (work + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -1162,6 +1369,32 @@ inline int grid_for(uint64_t work, int per_block, int max_blocks) {
 }
 
 }  // namespace
+
+namespace {
+
+void launch_overpartition(const LaunchEnv& e, const LevelParams& P, LevelSeg* segs, Src src,
+                          uint64_t* ssk, uint32_t* ssi, const Overpart& op) {
+  const uint32_t k = op.k, K = op.k * op.over;
+  cudaMemsetAsync(op.fine_cnt, 0, (size_t)K * 4, e.stream);
+  {
+    Scope sc(e, "L1.fine_count");
+    k_fine_count<<<e.num_sms, kFineThreads, fine_smem_bytes(K), e.stream>>>(
+        segs, src, ssk, ssi, op.over, P.no_tie_break, op.fine_cnt);
+  }
+  {
+    Scope sc(e, "L1.group");
+    k_group_greedy<<<1, kGreedyThreads, greedy_smem_bytes(K, k), e.stream>>>(
+        segs, ssk, ssi, op);
+  }
+}
+
+}  // namespace
+
+void launch_plain_groups(const LaunchEnv& e, const uint64_t* offsets, uint32_t k,
+                         uint64_t* fine_out, uint32_t* first_out) {
+  Scope sc(e, "L1.group");
+  k_plain_groups<<<(k + 256) / 256, 256, 0, e.stream>>>(offsets, k, fine_out, first_out);
+}
 
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
                        uint64_t n, uint32_t k1, int direct, uint64_t final_cap) {
@@ -1194,6 +1427,10 @@ void set_partition_kernel_attributes() {
     }
     g_wide_scatter_smem_max = limit;
   }
+  cudaFuncSetAttribute(k_fine_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fine_smem_bytes(kMaxFine));
+  cudaFuncSetAttribute(k_group_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)greedy_smem_bytes(kMaxFine, kMaxK));
   cudaGetLastError();  // a refused attribute only disables the variant
   const size_t w = umax64(wd_smem_bytes(kMaxK, 0), wd_smem_bytes(kMaxK, 1));
   cudaFuncSetAttribute(k_classify_count_wd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w);
@@ -1281,7 +1518,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
                   uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,
                   uint32_t* ssamp_idx, uint32_t* hist, uint32_t* block_sums, FinalItem* items,
                   int kmax_level, int last_level, int emit_final, uint64_t* offsets_out,
-                  uint64_t /*n_total*/, int unmap_out) {
+                  uint64_t /*n_total*/, int unmap_out, const Overpart* op) {
   const int par_in = P.level & 1;
   const int sms = e.num_sms;
   static const char* kNames[kMaxLevels + 1][10] = {
@@ -1315,7 +1552,8 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
     k_sample_merge_rank<<<grid_for(P.samp_cap, 256, sms * 8), 256, 0, e.stream>>>(
         st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
   }
-  const int mode = P.classifier;
+  if (op) launch_overpartition(e, P, segs, src, ssamp_key, ssamp_idx, *op);
+  const int mode = P.classifier | (P.no_tie_break ? 2 : 0);
   const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false, mode);
   const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true, mode);
   const int grid_c =

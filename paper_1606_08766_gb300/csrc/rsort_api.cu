@@ -106,10 +106,12 @@ struct Plan {
   int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
   int wide_scatter_k = 1024;  // levels with at least this many buckets use wide sub-tiles
   uint32_t target_bucket = kTargetBucket;  // automatic fan-out target
+  uint64_t samp_extra = 0;  // sorted-sample slots past the sample (overpartitioning)
+  uint64_t fine_cap = 0;    // fine partition counters (overpartitioning)
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
-  size_t off_list0 = 0, off_list1 = 0, off_items = 0, off_state = 0, total = 0;
+  size_t off_list0 = 0, off_list1 = 0, off_items = 0, off_state = 0, off_fine = 0, total = 0;
 };
 
 uint32_t ceil_log2_host(uint32_t k) {
@@ -133,8 +135,9 @@ void layout(Plan& p) {
   }
   p.off_samp_key = take(p.samp_cap * 8);
   p.off_samp_idx = take(p.samp_cap * 4);
-  p.off_ssamp_key = take(p.samp_cap * 8);
-  p.off_ssamp_idx = take(p.samp_cap * 4);
+  p.off_ssamp_key = take((p.samp_cap + p.samp_extra) * 8);
+  p.off_ssamp_idx = take((p.samp_cap + p.samp_extra) * 4);
+  p.off_fine = take(p.fine_cap * 4);
   p.off_hist = take(p.hist_cap * 4);
   p.off_sums = take((p.hist_cap / kScanTile + 2) * 4);
   p.off_segs = take(p.seg_cap * sizeof(LevelSeg));
@@ -544,11 +547,17 @@ rsort_status rsort_check(rsort_ctx* c) {
   return s;
 }
 
-rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
-                             uint64_t n, uint32_t k, uint64_t seed, void* d_keys_out,
-                             uint32_t* d_pos_out, uint64_t* d_offsets_out, void* stream) {
+namespace {
+
+rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                            uint64_t n, uint32_t k, uint64_t seed, uint32_t tie_break,
+                            uint32_t over, void* d_keys_out, uint32_t* d_pos_out,
+                            uint64_t* d_offsets_out, uint64_t* d_fine_out,
+                            uint32_t* d_first_out, void* stream) {
   if (!c || (type != RSORT_KEY_U64 && type != RSORT_KEY_F64)) return RSORT_EINVAL;
   if (k < 1 || k > (uint32_t)kMaxK || n > 0xFFFFFFFFull) return RSORT_EINVAL;
+  if (tie_break > 1 || over < 1 || (over > 1 && (uint64_t)k * over > (uint64_t)kMaxFine))
+    return RSORT_EINVAL;
   if (!d_offsets_out || (n > 0 && (!d_keys_in || !d_keys_out || !d_pos_out)))
     return RSORT_EINVAL;
   if (n > 0 && d_keys_in == d_keys_out) return RSORT_EINVAL;
@@ -562,9 +571,22 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   LaunchEnv e = env_of(c, s);
+  const uint32_t K = k * over;
   if (n == 0) {
-    // every bucket is empty
+    // every partition is empty; fine partition g is output g, or all fine
+    // partitions sit in output 0 when overpartitioned
     cudaMemsetAsync(d_offsets_out, 0, (size_t)(k + 1) * 8, s);
+    if (d_fine_out) cudaMemsetAsync(d_fine_out, 0, (size_t)K * 8, s);
+    if (d_first_out) {
+      if (over == 1) {
+        launch_plain_groups(e, d_offsets_out, k, nullptr, d_first_out);
+      } else {
+        std::vector<uint32_t> h(k + 1, K);
+        h[0] = 0;
+        cudaMemcpyAsync(d_first_out, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+      }
+    }
     return cuda_status(c);
   }
   Plan p;
@@ -576,6 +598,10 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
   p.need_tmp = false;
+  if (over > 1) {
+    p.samp_extra = (uint64_t)kk + 2;
+    p.fine_cap = K;
+  }
   layout(p);
   Workspace& ws = c->ws;
   rsort_status rs = ensure_workspace(c, ws, p.total, s);
@@ -584,15 +610,40 @@ rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_ke
   SegIn* list1 = at<SegIn>(ws, p.off_list1);
   launch_init_plain(e, st, list1, at<FinalItem>(ws, p.off_items), n, k, 0, p.final_cap);
   LevelParams P = level_params(p, 1, seed, (int)kk);
+  P.no_tie_break = tie_break ? 0 : 1;
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
+  Overpart op{k, over, at<uint32_t>(ws, p.off_fine), d_fine_out, d_first_out};
   launch_level(e, P, st, list1, at<SegIn>(ws, p.off_list0), at<LevelSeg>(ws, p.off_segs), src,
                dst, kWhereOut, at<uint64_t>(ws, p.off_samp_key), at<uint32_t>(ws, p.off_samp_idx),
                at<uint64_t>(ws, p.off_ssamp_key), at<uint32_t>(ws, p.off_ssamp_idx),
                at<uint32_t>(ws, p.off_hist), at<uint32_t>(ws, p.off_sums),
                at<FinalItem>(ws, p.off_items), (int)kk, 1, 0, d_offsets_out, n,
-               type == RSORT_KEY_F64);
+               type == RSORT_KEY_F64, over > 1 ? &op : nullptr);
+  if (over == 1 && (d_fine_out || d_first_out))
+    launch_plain_groups(e, d_offsets_out, k, d_fine_out, d_first_out);
   return cuda_status(c);
+}
+
+}  // namespace
+
+rsort_status rsort_partition(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                             uint64_t n, uint32_t k, uint64_t seed, void* d_keys_out,
+                             uint32_t* d_pos_out, uint64_t* d_offsets_out, void* stream) {
+  return partition_impl(c, type, d_keys_in, n, k, seed, 1, 1, d_keys_out, d_pos_out,
+                        d_offsets_out, nullptr, nullptr, stream);
+}
+
+rsort_status rsort_partition_ex(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
+                                uint64_t n, uint32_t k, uint64_t seed,
+                                const rsort_partition_opts* opts, void* d_keys_out,
+                                uint32_t* d_pos_out, uint64_t* d_offsets_out,
+                                uint64_t* d_fine_sizes_out, uint32_t* d_group_first_out,
+                                void* stream) {
+  const uint32_t tb = opts ? opts->tie_break : 1u;
+  const uint32_t over = opts ? opts->overpartition : 1u;
+  return partition_impl(c, type, d_keys_in, n, k, seed, tb, over, d_keys_out, d_pos_out,
+                        d_offsets_out, d_fine_sizes_out, d_group_first_out, stream);
 }
 
 rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,

@@ -19,6 +19,7 @@ constexpr int kWarpSpan = 32 * kItems;            // 512 consecutive keys per wa
 constexpr int kSubTile = kPartThreads * kItems;   // 4096 keys staged per sub-tile
 constexpr int kMaxK = 2048;                       // buckets per partition step
 constexpr int kMaxKDeep = 512;                    // buckets at levels >= 2
+constexpr int kMaxFine = 10240;                   // fine partitions of an overpartitioned step
 constexpr int kBucketCap = 4096;                  // T_s: largest bucket one CTA sorts
 constexpr int kTargetBucket = 640;                // aim for this final bucket size
                                                   // (mostly below the 1024-key class)
@@ -116,6 +117,18 @@ struct LevelParams {
   int warp_direct;        // 1: per-warp sub-chunks scattered straight to HBM
   int wide_scatter_k;     // levels with at least this many buckets scatter 4096-key sub-tiles
   uint32_t target_bucket; // automatic fan-out aims at buckets of this many keys
+  int no_tie_break = 0;   // 1: classify by key only (the NTB ablation)
+};
+
+// AMS-sort overpartitioning of a one-segment partition step: b*k fine
+// partitions are counted, grouped greedily into k outputs, and the k-1 group
+// boundaries become the splitters of the ordinary k-way step.
+struct Overpart {
+  uint32_t k;            // outputs (the segment's k)
+  uint32_t over;         // b >= 2
+  uint32_t* fine_cnt;    // [b*k] scratch counters (cleared by the launch)
+  uint64_t* fine_out;    // [b*k] fine partition sizes, or nullptr
+  uint32_t* first_out;   // [k+1] first fine partition of every output, or nullptr
 };
 
 // Element source / destination of a level.
@@ -274,11 +287,13 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
                   uint64_t* samp_key, uint32_t* samp_idx, uint64_t* ssamp_key,
                   uint32_t* ssamp_idx, uint32_t* hist, uint32_t* block_sums, FinalItem* items,
                   int kmax_level, int last_level, int emit_final, uint64_t* offsets_out,
-                  uint64_t n_total, int unmap_out);
+                  uint64_t n_total, int unmap_out, const Overpart* op = nullptr);
 void launch_init_segments(const LaunchEnv& e, DevState* st, const uint64_t* offsets,
                           uint32_t nseg, uint64_t n, SegIn* list_l1, FinalItem* items,
                           uint64_t seg_cap, uint64_t final_cap);
 void set_partition_kernel_attributes();
+void launch_plain_groups(const LaunchEnv& e, const uint64_t* offsets, uint32_t k,
+                         uint64_t* fine_out, uint32_t* first_out);
 void set_local_kernel_attributes();
 void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
                        uint64_t item_cap, const uint64_t* in_key, Dst out, Dst tmp, int f64);
