@@ -74,17 +74,28 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi needs a moment before its first sample: wait for it so
+            # that the samples kept (from mark() on) cover the timed region
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.first = 0
+
+    def mark(self):
+        """Samples before this call (start-up, warm-up) are not reported."""
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -102,7 +113,7 @@ class ClockSampler:
             self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in self.lines[self.first:]:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -353,6 +364,44 @@ def serving_leg(dev, requests=2000, lo_log2=4, hi_log2=20, seed=5):
             "poisson_rate_requests_s": rate, "p50_us": poi["p50_us"], "p99_us": poi["p99_us"]}
 
 
+def partition_leg(ctx, dev, n=1 << 26, k=1024, over=10, reps=3):
+    """The partition step alone on duplicate-heavy and unique inputs: the
+    robust step, the NTB ablation (classification by key only) and AMS
+    overpartitioning (b = 10: eps = 0.2 with one level).  Reports device time
+    and the largest partition over the mean n/k."""
+    import numpy as np
+    import torch
+
+    import instances
+
+    out = {"workload": f"one partition step, n=2^{n.bit_length() - 1}, k={k}, seed 1",
+           "variants": {"robust": "tie_break=1, b=1", "ntb": "tie_break=0, b=1",
+                        f"over{over}": f"tie_break=1, b={over}"}}
+    stream = torch.cuda.current_stream(dev)
+    for name in ("uniform", "zero", "deter_dupl", "rand_dupl"):
+        keys = torch.from_numpy(instances.generate(name, n, p=k, seed=1).view(np.int64)).to(dev)
+        row = {}
+        for label, kw in (("robust", {}), ("ntb", {"tie_break": False}),
+                          (f"over{over}", {"overpartition": over})):
+            ctx.partition_ex(keys, k, seed=1, **kw)
+            ts = []
+            for _ in range(reps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                res = ctx.partition_ex(keys, k, seed=1, **kw)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+            sizes = torch.diff(res[2]).max().item()
+            row[label] = {"ms": sorted(ts)[len(ts) // 2], "max_over_mean": sizes / (n / k)}
+            del res
+        out[name] = row
+        del keys
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_rsort(args):
     import numpy as np
     import torch
@@ -399,6 +448,7 @@ def run_rsort(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    clocks.mark()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -467,6 +517,7 @@ def run_rsort(args):
     extra = {}
     if rank == 0 and ws == 1 and not args.skip_systems:
         del keys_pin, out_pin, perm_pin
+        extra["partition_variants"] = partition_leg(ctx, dev)
         extra["batched"] = batched_leg(ctx, dev)
         torch.cuda.empty_cache()
         extra["serving"] = serving_leg(dev)
@@ -493,7 +544,7 @@ def run_rsort(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsort", choices=["rsort", "reference"])
     ap.add_argument("--skip-systems", action="store_true",
