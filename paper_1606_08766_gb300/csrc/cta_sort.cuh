@@ -30,8 +30,12 @@ static_assert(kRankMax <= kLocalThreads, "rank-by-counting holds one element per
 struct CtaSortSmem {
   uint64_t* k;     // [cap]      cap = NT * ITEMS
   uint32_t* i;     // [cap]
-  uint32_t* hist;  // [cap]      2*cap 16-bit bin counters, packed in pairs
+  uint32_t* hist;  // [cap + cap/2]  2*cap 16-bit bin counters packed in pairs,
+                   //                then the list of bins holding several elements
 };
+
+// Shared memory per element of capacity that a CtaSortSmem needs.
+constexpr int kCtaSortBytesPerElem = 8 + 4 + 4 + 2;
 
 template <int NT>
 __device__ __forceinline__ void block_minmax_u64(uint64_t& mn, uint64_t& mx, uint64_t* red) {
@@ -111,6 +115,8 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   const int bits = range ? 64 - __clzll((long long)range) : 0;
   const int shift = bits > lognb ? bits - lognb : 0;
   for (uint32_t w = tid; w < nb / 2; w += NT) s.hist[w] = 0;
+  __shared__ uint32_t s_nmulti;
+  if (tid == 0) s_nmulti = 0;
   __syncthreads();
   uint32_t bs[ITEMS];
 #pragma unroll
@@ -123,15 +129,19 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
   }
   __syncthreads();
-  // exclusive scan of the nb 16-bit counters (nb/2 words; each thread a run)
+  // exclusive scan of the nb 16-bit counters (nb/2 words; each thread a run),
+  // which also finds out whether any bin is crowded
   const uint32_t words = nb / 2;
   const uint32_t per = (words + NT - 1) / NT;
   const uint32_t w0 = tid * per;
+  bool crowd = false;
   {
     uint32_t loc = 0;
     for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
       const uint32_t v = s.hist[w];
-      loc += (v & 0xffffu) + (v >> 16);
+      const uint32_t a = v & 0xffffu, b = v >> 16;
+      loc += a + b;
+      crowd |= a > (uint32_t)kBinLimit || b > (uint32_t)kBinLimit;
     }
     uint64_t tot;
     uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
@@ -142,18 +152,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
       run = hi + (v >> 16);
     }
   }
-  __syncthreads();
-  bool crowded = false;
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    if (r * NT + tid < m) {
-      const uint32_t b = bs[r] >> 16;
-      const uint32_t lo = bin_start(s.hist, b);
-      const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
-      crowded |= (hi - lo) > (uint32_t)kBinLimit;
-    }
-  }
-  if (__syncthreads_or(crowded)) {
+  if (__syncthreads_or(crowd)) {
     // clustered keys: bitonic sort of the whole bucket
     const uint32_t P = next_pow2_u32(m);
 #pragma unroll
@@ -165,45 +164,44 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     block_bitonic_sort<NT>(s.k, s.i, (int)P);
     return;
   }
-  // counting-sort scatter into the bins
+  // counting-sort scatter into the bins; the second element to land in a bin
+  // puts the bin on the list of bins that still need ordering
+  uint32_t* multi = s.hist + kCap;
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     if (r * NT + tid < m) {
-      const uint32_t p = bin_start(s.hist, bs[r] >> 16) + (bs[r] & 0xffffu);
+      const uint32_t b = bs[r] >> 16, o = bs[r] & 0xffffu;
+      const uint32_t p = bin_start(s.hist, b) + o;
       s.k[p] = key[r];
       s.i[p] = idx[r];
+      if (o == 1) multi[atomicAdd(&s_nmulti, 1u)] = b;
     }
   }
   __syncthreads();
-  // rank by counting inside each bin; an element alone in its bin is final
-  constexpr uint32_t kInPlace = 0xffffffffu;
-  uint32_t fin[ITEMS];
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    fin[r] = kInPlace;
-    if (r * NT + tid < m) {
-      const uint32_t b = bs[r] >> 16;
-      const uint32_t lo = bin_start(s.hist, b);
-      const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
-      if (hi - lo > 1) {
-        uint32_t rank = 0;
-        for (uint32_t q = lo; q < hi; ++q)
-          rank += pair_less(s.k[q], s.i[q], key[r], idx[r]) ? 1u : 0u;
-        fin[r] = lo + rank;
+  // order every listed bin in place by insertion (at most kBinLimit elements;
+  // an element alone in its bin is already in its final slot)
+  const uint32_t nmulti = s_nmulti;
+  for (uint32_t j = tid; j < nmulti; j += NT) {
+    const uint32_t b = multi[j];
+    const uint32_t lo = bin_start(s.hist, b);
+    const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
+    uint64_t* bk = s.k + lo;
+    uint32_t* bi = s.i + lo;
+    for (uint32_t a = 1; a < hi - lo; ++a) {
+      const uint64_t ka = bk[a];
+      const uint32_t ia = bi[a];
+      uint32_t q = a;
+      while (q > 0 && pair_less(ka, ia, bk[q - 1], bi[q - 1])) {
+        bk[q] = bk[q - 1];
+        bi[q] = bi[q - 1];
+        --q;
       }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < ITEMS; ++r) {
-    if (fin[r] != kInPlace) {
-      s.k[fin[r]] = key[r];
-      s.i[fin[r]] = idx[r];
+      bk[q] = ka;
+      bi[q] = ia;
     }
   }
   __syncthreads();
   (void)kCap;
-  (void)w0;
 }
 
 }  // namespace rsort

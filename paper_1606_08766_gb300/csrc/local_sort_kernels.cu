@@ -227,9 +227,9 @@ static_assert(kLocalThreads * kLocalItems == kBucketCap, "medium class fits one 
 
 void set_local_kernel_attributes() {
   cudaFuncSetAttribute(k_local_sort<kSmallThreads, kSmallItems, kClassSmall>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * 16);
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * kCtaSortBytesPerElem);
   cudaFuncSetAttribute(k_local_sort<kLocalThreads, kLocalItems, kClassMedium>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * 16);
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * kCtaSortBytesPerElem);
   cudaFuncSetAttribute(k_local_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kBucketCap * 12);
 }
@@ -248,12 +248,12 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   {
     Scope sc(e, "local_sort");
     k_local_sort<kSmallThreads, kSmallItems, kClassSmall>
-        <<<e.num_sms * 6, kSmallThreads, kSmallCap * 16, e.stream>>>(st, items, item_cap, B);
+        <<<e.num_sms * 6, kSmallThreads, kSmallCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
   }
   {
     Scope sc(e, "local_sort_medium");
     k_local_sort<kLocalThreads, kLocalItems, kClassMedium>
-        <<<e.num_sms * 2, kLocalThreads, kBucketCap * 16, e.stream>>>(st, items, item_cap, B);
+        <<<e.num_sms * 2, kLocalThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
   }
   {
     Scope sc(e, "local_big");

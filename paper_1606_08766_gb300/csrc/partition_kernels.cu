@@ -1404,7 +1404,7 @@ void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem
 
 void set_partition_kernel_attributes() {
   cudaFuncSetAttribute(k_sample_sort_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kSampleChunk * (8 + 4 + 4));
+                       kSampleChunk * kCtaSortBytesPerElem);
   const size_t c = umax64(part_smem_bytes(kMaxK, false, 0), part_smem_bytes(kMaxK, false, 1));
   const size_t s = umax64(part_smem_bytes(kMaxK, true, 0), part_smem_bytes(kMaxK, true, 1));
   cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
@@ -1543,7 +1543,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   {
     Scope sc(e, nm[2]);
-    const int smem = kSampleChunk * (8 + 4 + 4);
+    const int smem = kSampleChunk * kCtaSortBytesPerElem;
     k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms), kSampleThreads, smem, e.stream>>>(
         st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
   }
