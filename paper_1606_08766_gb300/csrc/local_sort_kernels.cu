@@ -162,9 +162,14 @@ __device__ __forceinline__ int64_t next_item(DevState* st, int cls, uint64_t cap
   return it < umin64(st->nfinal_c[cls], cap) ? (int64_t)it : -1;
 }
 
+// Resident CTAs per SM of the small class: the sort is latency-bound per
+// bucket, so more buckets in flight per SM pay more than registers (10 CTAs
+// of 128 threads measured 17% faster than 6 at 2^28 keys).
+constexpr int kSmallPerSm = 10;
+
 // Buckets of up to NT*IT keys, sorted by one CTA each (cta_sort_pairs).
 template <int NT, int IT, int CLS>
-__global__ void __launch_bounds__(NT, (NT == 128 ? 6 : 2))
+__global__ void __launch_bounds__(NT, (NT == 128 ? kSmallPerSm : 2))
 k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   constexpr int kCap = NT * IT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,7 +253,7 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   {
     Scope sc(e, "local_sort");
     k_local_sort<kSmallThreads, kSmallItems, kClassSmall>
-        <<<e.num_sms * 6, kSmallThreads, kSmallCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
+        <<<e.num_sms * kSmallPerSm, kSmallThreads, kSmallCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
   }
   {
     Scope sc(e, "local_sort_medium");

@@ -480,6 +480,7 @@ struct PartSmem {
   uint32_t* hist;      // [K]   classify: counts;  scatter: running offsets
   uint32_t* sbase;     // [K+1] scatter: sub-tile bucket starts
   uint16_t* wcnt;      // [kPartWarps][cnt_stride(K)] scatter: per-warp counts / bases
+  uint32_t* dlt;       // scatter: [K] output position minus sub-tile run start, per bucket
   uint8_t* wwin;       // [kPartWarps][K] scatter: per-warp winner lane of each bucket
   unsigned char* buf;  // classify: kCStages key stages; scatter: two sub-tile buffers
 };
@@ -533,6 +534,7 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
   p = base + part_common_bytes(kmax, mode);
   s.sbase = nullptr;
   s.wcnt = nullptr;
+  s.dlt = nullptr;
   s.wwin = nullptr;
   if (scatter) {
     s.sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4 + 4;
@@ -554,6 +556,7 @@ __host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, in
   size_t b = part_common_bytes(kmax, mode);
   b += (size_t)(kmax + 1) * 4 + 4;
   b += (size_t)nw * cnt_stride(kmax) * 2;
+  b += (size_t)kmax * 4;
   b += (size_t)nw * kmax;
   b = (b + 15) & ~(size_t)15;
   return b + 2 * (size_t)st * (8 + 4 + 2);
@@ -566,6 +569,8 @@ __device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int
   p += (size_t)(kmax + 1) * 4 + 4;
   s.wcnt = (uint16_t*)p;
   p += (size_t)nw * cnt_stride(kmax) * 2;
+  s.dlt = (uint32_t*)p;
+  p += (size_t)kmax * 4;
   s.wwin = (uint8_t*)p;
   p += (size_t)nw * kmax;
   s.buf = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
@@ -837,32 +842,34 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         lrank[r] = c0 + __popc(peers & ltmask);
       }
       __syncthreads();
-      // per bucket: exclusive prefix over warps (in place) and the sub-tile total
-      for (uint32_t b = threadIdx.x; b < k; b += NT) {
-        uint32_t tot = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
-          sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
-          tot += cnt;
-        }
-        sm.sbase[b] = tot;
-      }
-      __syncthreads();
-      {  // exclusive scan of the k sub-tile totals (one thread per run of buckets)
+      {  // per bucket (each thread a run of buckets): exclusive prefix over the
+         // warps' counts, in place; an exclusive scan of the bucket totals then
+         // places every bucket's run in the sub-tile, and the running output
+         // offsets advance by the totals
         const uint32_t per = (k + NT - 1) / NT;
         const uint32_t bb0 = threadIdx.x * per;
         const uint32_t bb1 = bb0 + per < k ? bb0 + per : k;
         uint32_t loc = 0;
-        for (uint32_t b = bb0; b < bb1; ++b) loc += sm.sbase[b];
+        for (uint32_t b = bb0; b < bb1; ++b) {
+          uint32_t tot = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
+            sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
+            tot += cnt;
+          }
+          sm.sbase[b] = tot;
+          loc += tot;
+        }
         uint64_t tot;
         uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
         for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t t = sm.sbase[b];
           sm.sbase[b] = run;
+          sm.dlt[b] = sm.hist[b] - run;  // modulo 2^32: positions are below 2^32
+          sm.hist[b] += t;
           run += t;
         }
-        if (threadIdx.x == 0) sm.sbase[k] = len;
       }
       __syncthreads();
       // counting-sort the sub-tile by bucket into its own buffer
@@ -879,14 +886,11 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       __syncthreads();
       for (uint32_t q = threadIdx.x; q < len; q += NT) {
         const uint32_t b = B.b[q];
-        const uint64_t d = (uint64_t)sm.hist[b] + (q - sm.sbase[b]);
+        const uint64_t d = (uint32_t)(sm.dlt[b] + q);
         const uint64_t kv = B.key[q];
         st_keep_u64(dst.key + d, unmap_out ? ordered_to_f64(kv) : kv, pol_keep);
         st_keep_u32(dst.idx + d, B.idx[q], pol_keep);
       }
-      __syncthreads();
-      for (uint32_t b = threadIdx.x; b < k; b += NT)
-        sm.hist[b] += sm.sbase[b + 1] - sm.sbase[b];
     }
     cp_async_wait<0>();
   }
