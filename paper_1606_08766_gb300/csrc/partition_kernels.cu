@@ -469,7 +469,8 @@ k_sample_merge_rank(const DevState* st, const LevelSeg* segs, const uint64_t* sa
 
 // Shared-memory carve-up of the classify / scatter kernels.
 constexpr int kCT = 2048;                       // keys per classify pipeline stage
-constexpr int kCStages = 3;                     // classify stages (2 in flight)
+constexpr int kCStages = 3;                     // classify stages at level 1 (2 in flight)
+constexpr int kCStagesDeep = 2;                 // deeper levels: fewer stages, more CTAs per SM
 constexpr int kCItems = kCT / kPartThreads;     // 8 keys per lane per stage
 constexpr int kST = 2048;                       // keys per scatter sub-tile
 constexpr int kSItems = kST / kPartThreads;     // 8 keys per lane per sub-tile
@@ -498,6 +499,10 @@ __host__ __device__ inline size_t part_common_bytes(uint32_t kmax, int mode) {
   size_t b = (mode & 1) == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
   b += (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
   return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t classify_smem_bytes(uint32_t kmax, int mode, int stages) {
+  return part_common_bytes(kmax, mode) + (size_t)stages * kCT * 8;
 }
 
 __host__ __device__ inline size_t part_smem_bytes(uint32_t kmax, bool scatter, int mode) {
@@ -559,7 +564,7 @@ __host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, in
   b += (size_t)kmax * 4;
   b += (size_t)nw * kmax;
   b = (b + 15) & ~(size_t)15;
-  return b + 2 * (size_t)st * (8 + 4 + 2);
+  return b + 2 * ((size_t)st * (8 + 4 + 2) + 16);
 }
 
 __device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int mode, int nw) {
@@ -580,8 +585,12 @@ __device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int
 // Steps 4 + 5a: classify every element and count, per chunk of W elements,
 // how many fall into each bucket.  hist is laid out per segment bucket-major:
 // hist[hist_off + b * nchunks + chunk].  The chunk's keys stream through a
-// kCStages-deep cp.async pipeline of kCT-key stages in shared memory.
-__global__ void __launch_bounds__(kPartThreads, 3)
+// STAGES-deep cp.async pipeline of kCT-key stages in shared memory.  Level 1
+// (few long chunks) runs 3 stages at 3 CTAs per SM; deeper levels (many
+// short chunks, each loading its segment's splitters) measured faster with 2
+// stages at 4 CTAs per SM.
+template <int STAGES>
+__global__ void __launch_bounds__(kPartThreads, STAGES == 2 ? 4 : 3)
 k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
                  const uint32_t* ssi, uint32_t* hist, uint32_t W, uint32_t kmax, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -609,21 +618,21 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
       if (s < nst) {
         const uint64_t b0 = cs + s * kCT;
         const uint32_t len = (uint32_t)umin64(kCT, ce - b0);
-        uint64_t* dst = stage + (s % kCStages) * kCT;
+        uint64_t* dst = stage + (s % STAGES) * kCT;
         for (uint32_t t = threadIdx.x; t < len; t += kPartThreads)
           cp_async_8(dst + t, src.key + b0 + t, pol);
       }
       cp_async_commit();
     };
 #pragma unroll
-    for (int s = 0; s < kCStages - 1; ++s) issue(s);
+    for (int s = 0; s < STAGES - 1; ++s) issue(s);
     for (uint64_t s = 0; s < nst; ++s) {
-      cp_async_wait<kCStages - 2>();
+      cp_async_wait<STAGES - 2>();
       __syncthreads();
-      issue(s + kCStages - 1);
+      issue(s + STAGES - 1);
       const uint64_t b0 = cs + s * kCT;
       const uint32_t len = (uint32_t)umin64(kCT, ce - b0);
-      const uint64_t* stg = stage + (s % kCStages) * kCT;
+      const uint64_t* stg = stage + (s % STAGES) * kCT;
       const uint32_t q0 = (uint32_t)warp * (kCItems * 32) + lane;
       uint64_t key[kCItems];
 #pragma unroll
@@ -638,6 +647,11 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
         const uint64_t pos = b0 + q0 + r * 32;
         return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
       }, sm.sp);
+      if (src.bid) {
+#pragma unroll
+        for (int r = 0; r < kCItems; ++r)
+          if (q0 + r * 32 < len) src.bid[b0 + q0 + r * 32] = (uint16_t)bk[r];
+      }
 #pragma unroll
       for (int r = 0; r < kCItems; ++r) {
         const bool v = q0 + r * 32 < len;
@@ -728,7 +742,9 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
   constexpr int NW = NT / 32;
   constexpr int IT = ST / NT;
   static_assert(IT * 32 * NW == ST, "warp w owns IT*32 consecutive keys of a sub-tile");
-  constexpr size_t BUFB = (size_t)ST * (8 + 4 + 2);
+  // keys, positions, bucket ids (+16 bytes: the staged ids start at an even
+  // position, one before the sub-tile when it starts at an odd one)
+  constexpr size_t BUFB = (size_t)ST * (8 + 4 + 2) + 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PartSmem sm = carve_scatter(smem_raw, kmax, mode, NW);
   __shared__ uint64_t scan_sm[NW];
@@ -782,6 +798,13 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
           cp_async_8(B.key + t, src.key + b0 + t, pol);
           if (src.idx) cp_async_4(B.idx + t, src.idx + b0 + t, pol);
         }
+        if (src.bid) {  // bucket ids as 4-byte pairs from the even position at or below b0
+          const uint64_t w0 = b0 >> 1;
+          const uint32_t nw = (uint32_t)(((b0 + len + 1) >> 1) - w0);
+          const uint32_t* gw = reinterpret_cast<const uint32_t*>(src.bid) + w0;
+          for (uint32_t t = threadIdx.x; t < nw; t += NT)
+            cp_async_4(reinterpret_cast<uint32_t*>(B.b) + t, gw + t, pol);
+        }
       }
       cp_async_commit();
     };
@@ -806,7 +829,16 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
         idx[r] = v ? (src.idx ? B.idx[q] : (uint32_t)(b0 + q - sg.start)) : 0;
       }
-      classify_batch<IT>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
+      if (src.bid) {
+        const uint16_t* bh = B.b + (b0 & 1);
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+          const uint32_t q = q0 + r * 32;
+          bk[r] = q < len ? bh[q] : 0u;
+        }
+      } else {
+        classify_batch<IT>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
+      }
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
 #pragma unroll
@@ -1411,7 +1443,12 @@ void set_partition_kernel_attributes() {
                        kSampleChunk * kCtaSortBytesPerElem);
   const size_t c = umax64(part_smem_bytes(kMaxK, false, 0), part_smem_bytes(kMaxK, false, 1));
   const size_t s = umax64(part_smem_bytes(kMaxK, true, 0), part_smem_bytes(kMaxK, true, 1));
-  cudaFuncSetAttribute(k_classify_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
+  cudaFuncSetAttribute(k_classify_count<kCStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)c);
+  cudaFuncSetAttribute(k_classify_count<kCStagesDeep>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)umax64(classify_smem_bytes(kMaxKDeep, 0, kCStagesDeep),
+                                   classify_smem_bytes(kMaxKDeep, 1, kCStagesDeep)));
   (void)s;
   cudaFuncSetAttribute(k_scatter<kPartThreads, 2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)umax64(scatter_smem_bytes(kMaxK, 0, kPartWarps, 2048),
@@ -1460,7 +1497,15 @@ int part_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
                                                   kPartThreads,
                                                   scatter_smem_bytes(kmax, mode, kPartWarps, 2048));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count, kPartThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count<kCStages>, kPartThreads,
+                                                  smem);
+  return nb > 0 ? nb : 1;
+}
+
+int classify_deep_blocks_per_sm(uint32_t kmax, int mode) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count<kCStagesDeep>, kPartThreads,
+                                                classify_smem_bytes(kmax, mode, kCStagesDeep));
   return nb > 0 ? nb : 1;
 }
 
@@ -1560,8 +1605,13 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   const int mode = P.classifier | (P.no_tie_break ? 2 : 0);
   const size_t smem_c = part_smem_bytes((uint32_t)kmax_level, false, mode);
   const size_t smem_s = part_smem_bytes((uint32_t)kmax_level, true, mode);
-  const int grid_c =
-      grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, false, mode));
+  // deeper levels take the 2-stage classify when their buckets fit its shared memory
+  const bool deep_c = P.level > 1 && (uint32_t)kmax_level <= (uint32_t)kMaxKDeep;
+  const size_t smem_cd = classify_smem_bytes((uint32_t)kmax_level, mode, kCStagesDeep);
+  const int grid_c = grid_for(
+      P.chunk_cap, 1,
+      sms * (deep_c ? classify_deep_blocks_per_sm((uint32_t)kmax_level, mode)
+                    : part_blocks_per_sm((uint32_t)kmax_level, false, mode)));
   const int grid_s =
       grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode));
   const size_t smem_wd = wd_smem_bytes((uint32_t)kmax_level, mode);
@@ -1569,13 +1619,24 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, false, mode));
   const int grid_wd_s =
       grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, true, mode));
+  const bool wide = !P.warp_direct && kmax_level >= P.wide_scatter_k &&
+                    scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096) <=
+                        g_wide_scatter_smem_max;
+  // Stored bucket ids spare the staged scatter its second classification.
+  // The warp-direct scatter classifies again, and so does the wide one: with
+  // 1024+ buckets its L2-resident write frontiers are the bottleneck, and the
+  // extra id stream measured slower there (4.04 vs 3.82 ms at 2^28 keys).
+  if (P.warp_direct || wide) src.bid = nullptr;
   {
     Scope sc(e, nm[4]);
     if (P.warp_direct)
       k_classify_count_wd<<<grid_wd_c, kPartThreads, smem_wd, e.stream>>>(
           st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
+    else if (deep_c)
+      k_classify_count<kCStagesDeep><<<grid_c, kPartThreads, smem_cd, e.stream>>>(
+          st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
     else
-      k_classify_count<<<grid_c, kPartThreads, smem_c, e.stream>>>(
+      k_classify_count<kCStages><<<grid_c, kPartThreads, smem_c, e.stream>>>(
           st, segs, src, ssamp_key, ssamp_idx, hist, P.W, (uint32_t)kmax_level, mode);
   }
   const int scan_grid = (int)((P.hist_cap + kScanTile - 1) / kScanTile);
@@ -1597,8 +1658,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       k_scatter_wd<<<grid_wd_s, kPartThreads, smem_wd, e.stream>>>(
           st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
           mode);
-    else if (kmax_level >= P.wide_scatter_k &&
-             scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096) <= g_wide_scatter_smem_max)
+    else if (wide)
       k_scatter<512, 4096><<<grid_for(P.chunk_cap, 1,
                                       sms * wide_scatter_blocks_per_sm((uint32_t)kmax_level, mode)),
                              512, scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096),

@@ -111,7 +111,8 @@ struct Plan {
   // arena offsets
   size_t off_tmp_key = 0, off_tmp_idx = 0, off_samp_key = 0, off_samp_idx = 0;
   size_t off_ssamp_key = 0, off_ssamp_idx = 0, off_hist = 0, off_sums = 0, off_segs = 0;
-  size_t off_list0 = 0, off_list1 = 0, off_items = 0, off_state = 0, off_fine = 0, total = 0;
+  size_t off_list0 = 0, off_list1 = 0, off_items = 0, off_state = 0, off_fine = 0, off_bid = 0;
+  size_t total = 0;
 };
 
 uint32_t ceil_log2_host(uint32_t k) {
@@ -138,6 +139,7 @@ void layout(Plan& p) {
   p.off_ssamp_key = take((p.samp_cap + p.samp_extra) * 8);
   p.off_ssamp_idx = take((p.samp_cap + p.samp_extra) * 4);
   p.off_fine = take(p.fine_cap * 4);
+  p.off_bid = take((p.n + 16) * 2);
   p.off_hist = take(p.hist_cap * 4);
   p.off_sums = take((p.hist_cap / kScanTile + 2) * 4);
   p.off_segs = take(p.seg_cap * sizeof(LevelSeg));
@@ -259,6 +261,7 @@ void enqueue_levels_and_local(rsort_ctx* c, Workspace& ws, const Plan& p, const 
       const Dst& prev = ((L - 1) & 1) ? tmp : out;
       src = Src{prev.key, prev.idx, 0};
     }
+    src.bid = at<uint16_t>(ws, p.off_bid);
     const Dst& dst = (L & 1) ? tmp : out;
     const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
     launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(ws, p.off_segs), src,
@@ -612,6 +615,7 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   LevelParams P = level_params(p, 1, seed, (int)kk);
   P.no_tie_break = tie_break ? 0 : 1;
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
+  src.bid = at<uint16_t>(ws, p.off_bid);
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
   Overpart op{k, over, at<uint32_t>(ws, p.off_fine), d_fine_out, d_first_out};
   launch_level(e, P, st, list1, at<SegIn>(ws, p.off_list0), at<LevelSeg>(ws, p.off_segs), src,

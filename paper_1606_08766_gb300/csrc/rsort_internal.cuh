@@ -136,6 +136,9 @@ struct Src {
   const uint64_t* key;
   const uint32_t* idx;  // nullptr: the original position is implicit
   int map_f64;          // keys need the float64 order map on load
+  // [n + 16] bucket of every element by position, written by the classify
+  // pass and read by the scatter (nullptr: the scatter classifies again)
+  uint16_t* bid = nullptr;
 };
 struct Dst {
   uint64_t* key;
