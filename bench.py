@@ -50,6 +50,11 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
+    "L1.scatter": 34.13,   # 1.0713 GB read + 1.2191 GB write at 2^26 keys
+    "L2.scatter": 26.33,   # 1.0114 + 0.7558 GB
+    "local_sort": 22.70,   # 0.7879 + 0.7355 GB
+    "L1.classify": 8.07,   # 0.5374 + 0.0042 GB
+    "L2.classify": 9.69,   # 0.5718 + 0.0783 GB
 }
 
 

@@ -375,9 +375,19 @@ k_sample(const DevState* st, const LevelSeg* segs, Src src, uint64_t* samp_key,
          uint32_t* samp_idx) {
   const uint64_t total = st->total_samples;
   const uint32_t G = st->cur_nseg;
-  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+  // every CTA draws a contiguous range of samples, so a thread's segment
+  // changes rarely and the segment search runs once per segment, not per sample
+  const uint64_t span = (total + gridDim.x - 1) / gridDim.x;
+  const uint64_t s0 = (uint64_t)blockIdx.x * span;
+  const uint64_t s1 = umin64(total, s0 + span);
+  uint32_t g = 0;
+  uint64_t g_lo = 1, g_hi = 0;  // sample range of the cached segment (empty)
+  for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    if (s < g_lo || s >= g_hi) {
+      g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+      g_lo = segs[g].samp_off;
+      g_hi = g_lo + segs[g].S;
+    }
     const LevelSeg& sg = segs[g];
     const uint64_t j = s - sg.samp_off;
     const uint64_t lo = (j * sg.m) / sg.S, hi = ((j + 1) * sg.m) / sg.S;
@@ -440,9 +450,18 @@ k_sample_merge_rank(const DevState* st, const LevelSeg* segs, const uint64_t* sa
                     const uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
   const uint64_t total = st->total_samples;
   const uint32_t G = st->cur_nseg;
-  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total;
-       s += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+  // contiguous sample range per CTA, segment searched once per segment
+  const uint64_t span = (total + gridDim.x - 1) / gridDim.x;
+  const uint64_t s0 = (uint64_t)blockIdx.x * span;
+  const uint64_t s1 = umin64(total, s0 + span);
+  uint32_t g = 0;
+  uint64_t g_lo = 1, g_hi = 0;
+  for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    if (s < g_lo || s >= g_hi) {
+      g = find_seg(segs, G, s, [](const LevelSeg& x) { return x.samp_off; });
+      g_lo = segs[g].samp_off;
+      g_hi = g_lo + segs[g].S;
+    }
     const LevelSeg& sg = segs[g];
     if (sg.nschunks <= 1) continue;
     const uint64_t j = s - sg.samp_off;
