@@ -136,20 +136,13 @@ __device__ void sort_big(const Bufs& B, const FinalItem& f, uint64_t* sk, uint32
 }
 
 template <int NT, int IT>
-__device__ __forceinline__ void sort_bucket(const Bufs& B, const FinalItem& f,
-                                            const CtaSortSmem& s, uint64_t* red,
-                                            uint64_t* scan_sm) {
-  const uint32_t m = f.size;
-  uint64_t key[IT];
-  uint32_t idx[IT];
+__device__ __forceinline__ void load_bucket(const Bufs& B, const FinalItem& f,
+                                            uint64_t (&key)[IT], uint32_t (&idx)[IT]) {
 #pragma unroll
   for (int r = 0; r < IT; ++r) {
     const uint32_t e = r * NT + threadIdx.x;
-    if (e < m) load_elem(B, f, e, key[r], idx[r]);
+    if (e < f.size) load_elem(B, f, e, key[r], idx[r]);
   }
-  cta_sort_pairs<NT, IT>(key, idx, m, true, s, red, scan_sm);
-  for (uint32_t t = threadIdx.x; t < m; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
-  __syncthreads();
 }
 
 // Next item of size class cls for this CTA (atomic work counter), or -1.
@@ -181,10 +174,28 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   __shared__ uint64_t scan_sm[NT / 32];
   __shared__ uint32_t s_item;
   const FinalItem* list = items + (uint64_t)CLS * cap;
-  for (;;) {
-    const int64_t it = next_item(st, CLS, cap, &s_item);
-    if (it < 0) break;
-    sort_bucket<NT, IT>(B, list[it], s, red, scan_sm);
+  uint64_t key[IT];
+  uint32_t idx[IT];
+  int64_t it = next_item(st, CLS, cap, &s_item);
+  FinalItem f{};
+  if (it >= 0) {
+    f = list[it];
+    load_bucket<NT, IT>(B, f, key, idx);
+  }
+  while (it >= 0) {
+    cta_sort_pairs<NT, IT>(key, idx, f.size, true, s, red, scan_sm);
+    // claim and start loading the next bucket before this one is stored, so
+    // its loads are in flight while the stores go out
+    const int64_t it2 = next_item(st, CLS, cap, &s_item);
+    FinalItem f2{};
+    if (it2 >= 0) {
+      f2 = list[it2];
+      load_bucket<NT, IT>(B, f2, key, idx);
+    }
+    for (uint32_t t = threadIdx.x; t < f.size; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
+    __syncthreads();
+    it = it2;
+    f = f2;
   }
 }
 
