@@ -66,6 +66,9 @@ def _load():
                                                 ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                                 ctypes.c_uint32, u64p, u32p, u64p, u32p, u64p]
             lib.oracle_partition_ex.restype = ctypes.c_int
+            lib.oracle_tree_median.argtypes = [u64p, ctypes.c_uint64, ctypes.c_int,
+                                               ctypes.c_uint32, ctypes.c_uint64]
+            lib.oracle_tree_median.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -180,3 +183,12 @@ def partition_ex(keys, k: int, seed: int, key_type: int = KEY_U64, tie_break: bo
     for name in ("keys_out", "pos_out"):
         out[name] = out[name][:n]
     return out
+
+
+def tree_median(keys, k: int, seed: int, key_type: int = KEY_U64) -> int:
+    """Binary-tree median approximation: the position of the chosen element."""
+    kb = _as_bits(keys)
+    r = _load().oracle_tree_median(_p64(kb), kb.shape[0], key_type, k, seed & (2**64 - 1))
+    if r < 0:
+        raise ValueError("oracle_tree_median rejected its arguments")
+    return int(r)

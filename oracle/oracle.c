@@ -38,6 +38,13 @@
  *                      output; Section 3 "AMS-sort", Appendix "Implementation
  *                      Details").
  *
+ *   oracle_tree_median The binary-tree median approximation of Section 3
+ *                      ("Approximate Median Selection with a Single
+ *                      Reduction"): leaves forward k-entry windows around
+ *                      their median, internal nodes merge and forward the
+ *                      middle k, the root flips a coin between its two middle
+ *                      entries.
+ *
  * Readings where the paper is silent (each also listed in the design doc):
  *   - phi: 64-bit floating-point elements (Appendix "Experimental Results") are
  *     ordered by their IEEE-754 bit pattern mapped to an unsigned integer
@@ -59,6 +66,12 @@
  *     (j = 1..b*k-1) is sorted sample floor(j*S/(b*k)); "a greedy algorithm
  *     ... minimizing the load imbalance" is read as: the smallest bound L for
  *     which the in-order greedy scan needs at most k groups, then that scan.
+ *   - tree median: leaves are the elements in input order (callers shuffle
+ *     if they need randomly permuted input), padded with empty leaves to a
+ *     power of two; an empty leaf forwards k/2 entries below and k/2 above
+ *     every element (its undefined positions); coins are bit 0 of
+ *     splitmix64(seed, leaf) and, at the root, splitmix64(seed, leaves); an
+ *     undefined root choice moves to the nearest element of the root window.
  *
  * parity pins: see tests/test_oracle_pins.py.  All functions are pinned.
  */
@@ -488,4 +501,116 @@ done:
     free(first);
     free(cnt);
     return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Binary-tree median approximation (Section 3, "Approximate Median         */
+/* Selection with a Single Reduction")                                      */
+/* ---------------------------------------------------------------------- */
+
+/* A window entry: tag -1 is "undefined on the left" (below every element),
+ * +1 "undefined on the right" (above every element), 0 an element (key,
+ * position).  Entries are ordered by tag, then (key, position). */
+typedef struct {
+    int tag;
+    uint64_t key;
+    uint32_t pos;
+} tm_entry;
+
+static int tm_less(const tm_entry *a, const tm_entry *b)
+{
+    if (a->tag != b->tag)
+        return a->tag < b->tag;
+    if (a->tag != 0)
+        return 0;
+    return pair_less(a->key, a->pos, b->key, b->pos);
+}
+
+/* Window that a leaf holding m in {0, 1} elements forwards: its sorted data
+ * a[1..m] read at positions c-k/2+1 .. c+k/2, c = floor(m/2) or (for odd m,
+ * by the coin) ceil(m/2), undefined positions left of 1 as -inf and right of
+ * m as +inf. */
+static void tm_leaf(tm_entry *w, uint32_t k, int m, uint64_t key, uint32_t pos, int coin)
+{
+    long c = (m % 2 == 1 && coin) ? (m + 1) / 2 : m / 2;
+    for (uint32_t t = 0; t < k; ++t) {
+        long at = c - (long)(k / 2) + 1 + (long)t; /* 1-based position */
+        if (at < 1) {
+            w[t].tag = -1;
+        } else if (at > m) {
+            w[t].tag = 1;
+        } else {
+            w[t].tag = 0;
+            w[t].key = key;
+            w[t].pos = pos;
+        }
+    }
+}
+
+/* Approximate median of keys[0..n) (n >= 1) with even window size k >= 2.
+ * Leaf i (i < P = next power of two >= n) holds element i, or nothing when
+ * i >= n.  Internal nodes merge their children's k-entry windows and forward
+ * the middle k of the 2k merged entries; the root returns entry k/2 or k/2+1
+ * (1-based) of its window.  Coins: leaf i uses bit 0 of splitmix64(seed, i),
+ * the root bit 0 of splitmix64(seed, P).  When the chosen entry is undefined
+ * (possible only when n is tiny next to k), the defined entry of the root
+ * window nearest to the middle is returned.  Returns the position of the
+ * chosen element, or -1 on bad arguments. */
+int64_t oracle_tree_median(const uint64_t *keys_bits, uint64_t n, int key_type, uint32_t k,
+                           uint64_t seed)
+{
+    if (n == 0 || n > 0xFFFFFFFFULL || k < 2 || (k & 1) || (key_type != 0 && key_type != 1))
+        return -1;
+    uint64_t P = 1;
+    while (P < n)
+        P <<= 1;
+    tm_entry *lvl = (tm_entry *)malloc(P * k * sizeof(tm_entry));
+    tm_entry *nxt = (tm_entry *)malloc((P / 2 + 1) * k * sizeof(tm_entry));
+    tm_entry *mrg = (tm_entry *)malloc(2 * (size_t)k * sizeof(tm_entry));
+    int64_t res = -1;
+    if (!lvl || !nxt || !mrg)
+        goto done;
+    for (uint64_t i = 0; i < P; ++i) {
+        int m = i < n ? 1 : 0;
+        uint64_t key = i < n ? phi(keys_bits[i], key_type) : 0;
+        tm_leaf(lvl + i * k, k, m, key, (uint32_t)i, (int)(oracle_splitmix64_at(seed, i) & 1));
+    }
+    for (uint64_t cnt = P; cnt > 1; cnt /= 2) {
+        for (uint64_t j = 0; j < cnt / 2; ++j) {
+            /* merge the two sorted windows of children 2j and 2j+1 */
+            const tm_entry *a = lvl + (2 * j) * k, *b = lvl + (2 * j + 1) * k;
+            uint32_t ia = 0, ib = 0;
+            for (uint32_t t = 0; t < 2 * k; ++t) {
+                if (ib >= k || (ia < k && !tm_less(&b[ib], &a[ia])))
+                    mrg[t] = a[ia++];
+                else
+                    mrg[t] = b[ib++];
+            }
+            /* middle k of the 2k merged entries: positions k/2+1 .. 3k/2 */
+            for (uint32_t t = 0; t < k; ++t)
+                nxt[j * k + t] = mrg[k / 2 + t];
+        }
+        tm_entry *tmp = lvl;
+        lvl = nxt;
+        nxt = tmp;
+    }
+    {
+        int coin = (int)(oracle_splitmix64_at(seed, P) & 1);
+        long pick = coin ? (long)(k / 2) : (long)(k / 2) - 1; /* 0-based */
+        for (long d = 0; d < (long)k; ++d) {
+            long cand[2] = {pick - d, pick + d};
+            for (int s = 0; s < 2; ++s) {
+                if (cand[s] >= 0 && cand[s] < (long)k && lvl[cand[s]].tag == 0) {
+                    res = (int64_t)lvl[cand[s]].pos;
+                    goto done;
+                }
+            }
+        }
+        res = 0;
+    }
+done:
+    free(lvl);
+    free(nxt);
+    free(mrg);
+    return res;
 }
