@@ -138,6 +138,29 @@ rsort_status rsort_partition_ex(rsort_ctx *ctx, rsort_key_type type, const void 
                                 uint64_t *d_fine_sizes_out, uint32_t *d_group_first_out,
                                 void *stream);
 
+/* Binary-tree median approximation (Section 3, "Approximate Median Selection
+ * with a Single Reduction"; the pivot rule of the paper's robust quicksort).
+ * Leaf i holds element i (in the order given; shuffle first for the paper's
+ * randomly permuted input), the leaves are padded with empty ones to a power
+ * of two P, and every node forwards a window of k entries:
+ *   - a leaf with one element: its element with k/2 entries below it and
+ *     k/2 - 1 above (coin 0) or k/2 - 1 below and k/2 above (coin 1);
+ *   - an empty leaf: k/2 entries below and k/2 above every element;
+ *   - an internal node: the middle k of its children's 2k merged entries.
+ * The root returns its window entry k/2 (coin 0) or k/2 + 1 (coin 1, 1-based),
+ * moving to the nearest element when that entry is not one.
+ *   - Coins: bit 0 of splitmix64(seed, i) for leaf i, of splitmix64(seed, P)
+ *     at the root.
+ *   - Elements are ordered by (key, position); float64 keys by their mapped
+ *     IEEE bit pattern.
+ * d_keys [n] (1 <= n <= 2^24, device); k in {2, 4, 8, 16, 32}; *d_pos_out
+ * (device u64) receives the position of the chosen element.  One CTA
+ * reduces the tree through the context's scratch (24 bytes per leaf).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+rsort_status rsort_approx_median(rsort_ctx *ctx, rsort_key_type type, const void *d_keys,
+                                 uint64_t n, uint32_t k, uint64_t seed, uint64_t *d_pos_out,
+                                 void *stream);
+
 /* Plain sort (Section 2's output contract): keys_out[j] = keys_in[perm[j]] with
  * (key, perm[j]) strictly increasing.  Large inputs run the multi-level robust
  * sample sort (level 1 with k = p_virtual buckets, deeper levels until buckets
@@ -278,6 +301,10 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                rsort_submit); fixed once the runtime has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
  *                (64..4096, default 640).
+ *   medium_sort  buckets of 1025..4096 keys: 0 (default) equal-width bins and
+ *                rank-by-counting; 1 in-SM quicksort whose pivots are the
+ *                binary-tree median approximation (see rsort_approx_median)
+ *                of a 256-element stratified sample of each segment.
  *   wide_scatter_k  levels with at least this many buckets stage 4096-key
  *                sub-tiles with 512 threads when shared memory allows
  *                (default 1024).

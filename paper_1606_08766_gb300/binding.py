@@ -94,6 +94,7 @@ def load_library(build_if_missing: bool = True):
         "rsort_partition": (i32, [vp, i32, vp, u64, u32, u64, vp, vp, vp, vp]),
         "rsort_partition_ex": (i32, [vp, i32, vp, u64, u32, u64, ctypes.POINTER(_PartOpts),
                                      vp, vp, vp, vp, vp, vp]),
+        "rsort_approx_median": (i32, [vp, i32, vp, u64, u32, u64, vp, vp]),
         "rsort_sort": (i32, [vp, i32, vp, vp, vp, u64, u32, u64, vp, ctypes.POINTER(_Stats)]),
         "rsort_segmented": (i32, [vp, i32, vp, vp, vp, u64, vp, u32, u64, vp]),
         "rsort_partition_noalloc": (i32, [i32, vp, u64, u32, u64, vp, vp, vp, vp]),
@@ -275,6 +276,18 @@ class Context:
                                           _stream_handle(stream))
         _check(rc, "rsort_partition_ex")
         return keys_out, pos_out, offsets, fine[:k * overpartition], first
+
+    def approx_median(self, keys: torch.Tensor, k: int = 16, seed: int = 1, key_type=None,
+                      stream=None) -> torch.Tensor:
+        """Binary-tree median approximation: a device int64 tensor holding the
+        position of the chosen element."""
+        _check_keys(keys)
+        out = torch.empty(1, dtype=torch.int64, device=keys.device)
+        rc = self._lib.rsort_approx_median(self._ctx, _key_type(keys, key_type), _ptr(keys),
+                                           keys.numel(), k, seed & (2**64 - 1), _ptr(out),
+                                           _stream_handle(stream))
+        _check(rc, "rsort_approx_median")
+        return out
 
     def check(self):
         _check(self._lib.rsort_check(self._ctx), "rsort_check")

@@ -65,6 +65,9 @@ struct rsort_ctx {
   // tunable "target_bucket": automatic fan-outs aim at final buckets of this
   // many keys (mostly below the 1024-key in-SM size class)
   uint32_t target_bucket = rsort::kTargetBucket;
+  // tunable "medium_sort": buckets of 1025..4096 keys are sorted by the
+  // equal-width bins (0, default) or by quicksort with tree-median pivots (1)
+  int medium_sort = 0;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

@@ -12,6 +12,7 @@
 //
 // Buckets are taken from a device work list with an atomic cursor by a
 // persistent grid.  The final store restores float64 bit patterns.
+#include "cta_quicksort.cuh"
 #include "cta_sort.cuh"
 #include "rsort_internal.cuh"
 
@@ -199,6 +200,36 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   }
 }
 
+// The medium class sorted by quicksort instead (tunable "medium_sort" = 1):
+// pivots from the binary-tree median approximation of a sample of every
+// segment (cta_quicksort.cuh).  The result is the same; the bins of
+// cta_sort_pairs measured faster, so this is an alternative, not the default.
+template <int NT, int CAP, int CLS>
+__global__ void __launch_bounds__(NT, 2)
+k_local_quicksort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B, uint64_t seed) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const QsSmem q = qs_carve(smem_raw, CAP);
+  __shared__ uint64_t scan_sm[NT / 32];
+  __shared__ uint32_t s_item;
+  const FinalItem* list = items + (uint64_t)CLS * cap;
+  for (;;) {
+    const int64_t it = next_item(st, CLS, cap, &s_item);
+    if (it < 0) break;
+    const FinalItem f = list[it];
+    for (uint32_t t = threadIdx.x; t < f.size; t += NT) {
+      uint64_t k;
+      uint32_t i;
+      load_elem(B, f, t, k, i);
+      q.ak[t] = k;
+      q.ai[t] = i;
+    }
+    __syncthreads();
+    cta_quicksort_pairs<NT>(q, f.size, splitmix64_at(seed, (uint64_t)it), scan_sm);
+    for (uint32_t t = threadIdx.x; t < f.size; t += NT) store_out(B, f.start + t, q.ak[t], q.ai[t]);
+    __syncthreads();
+  }
+}
+
 // Copy-through buckets (size 1, or equality buckets already in position
 // order): a coalesced copy that restores float64 bit patterns.
 __global__ void __launch_bounds__(256)
@@ -246,6 +277,8 @@ void set_local_kernel_attributes() {
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * kCtaSortBytesPerElem);
   cudaFuncSetAttribute(k_local_sort<kLocalThreads, kLocalItems, kClassMedium>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * kCtaSortBytesPerElem);
+  cudaFuncSetAttribute(k_local_quicksort<kLocalThreads, kBucketCap, kClassMedium>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs_smem_bytes(kBucketCap));
   cudaFuncSetAttribute(k_local_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kBucketCap * 12);
 }
@@ -268,8 +301,14 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   }
   {
     Scope sc(e, "local_sort_medium");
-    k_local_sort<kLocalThreads, kLocalItems, kClassMedium>
-        <<<e.num_sms * 2, kLocalThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
+    if (e.medium_sort == 1)
+      k_local_quicksort<kLocalThreads, kBucketCap, kClassMedium>
+          <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kBucketCap), e.stream>>>(
+              st, items, item_cap, B, 0x9e3779b97f4a7c15ULL);
+    else
+      k_local_sort<kLocalThreads, kLocalItems, kClassMedium>
+          <<<e.num_sms * 2, kLocalThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(
+              st, items, item_cap, B);
   }
   {
     Scope sc(e, "local_big");

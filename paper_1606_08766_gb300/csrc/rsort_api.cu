@@ -295,6 +295,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->target_bucket = (uint32_t)v;
     return RSORT_OK;
   }
+  if (strcmp(name, "medium_sort") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->medium_sort = (int)v;
+    return RSORT_OK;
+  }
   if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
   if (strcmp(name, "serve_slots") == 0) {
     if (v < 1 || v > 8) return RSORT_EINVAL;
@@ -325,6 +330,7 @@ LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   e.num_sms = c->num_sms;
   e.timer = c->profiling ? &c->timer : nullptr;
   e.launches = &c->launches;
+  e.medium_sort = c->medium_sort;
   return e;
 }
 
@@ -650,6 +656,30 @@ rsort_status rsort_partition_ex(rsort_ctx* c, rsort_key_type type, const void* d
                         d_offsets_out, d_fine_sizes_out, d_group_first_out, stream);
 }
 
+rsort_status rsort_approx_median(rsort_ctx* c, rsort_key_type type, const void* d_keys,
+                                 uint64_t n, uint32_t k, uint64_t seed, uint64_t* d_pos_out,
+                                 void* stream) {
+  if (!c || (type != RSORT_KEY_U64 && type != RSORT_KEY_F64)) return RSORT_EINVAL;
+  if (n < 1 || n > (1ull << 24) || !d_keys || !d_pos_out) return RSORT_EINVAL;
+  if (k != 2 && k != 4 && k != 8 && k != 16 && k != 32) return RSORT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->latched != RSORT_OK) {
+    rsort_status s = c->latched;
+    c->latched = RSORT_OK;
+    return s;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  LaunchEnv e = env_of(c, s);
+  rsort_status rs = ensure_workspace(c, c->ws, tree_median_scratch_bytes(n), s);
+  if (rs != RSORT_OK) return latch(c, rs);
+  if (!launch_tree_median(e, (const uint64_t*)d_keys, (uint32_t)n, type == RSORT_KEY_F64, k,
+                          seed, c->ws.arena, d_pos_out))
+    return RSORT_EINVAL;
+  return cuda_status(c);
+}
+
 rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in,
                         void* d_keys_out, uint32_t* d_perm_out, uint64_t n, uint32_t p_virtual,
                         uint64_t seed, void* stream, rsort_stats* opt_stats) {
@@ -790,6 +820,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "target_bucket") == 0) {
     *value = c->target_bucket;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "medium_sort") == 0) {
+    *value = c->medium_sort;
     return RSORT_OK;
   }
   if (strcmp(name, "serve_batch_keys") == 0) {

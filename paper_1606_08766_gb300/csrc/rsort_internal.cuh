@@ -281,6 +281,7 @@ struct LaunchEnv {
   int num_sms;
   KernelTimer* timer;   // may be null
   uint64_t* launches;   // launch counter
+  int medium_sort = 0;  // in-SM sort of buckets of 1025..4096 keys: 0 bins, 1 quicksort
 };
 
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
@@ -295,6 +296,11 @@ void launch_init_segments(const LaunchEnv& e, DevState* st, const uint64_t* offs
                           uint32_t nseg, uint64_t n, SegIn* list_l1, FinalItem* items,
                           uint64_t seg_cap, uint64_t final_cap);
 void set_partition_kernel_attributes();
+// Binary-tree median approximation of n <= 2^24 keys (median_kernels.cu);
+// k in {2, 4, 8, 16, 32}.  Returns false for an unsupported k.
+size_t tree_median_scratch_bytes(uint64_t n);
+bool launch_tree_median(const LaunchEnv& e, const uint64_t* keys, uint32_t n, int f64,
+                        uint32_t k, uint64_t seed, void* scratch, uint64_t* out_pos);
 void launch_plain_groups(const LaunchEnv& e, const uint64_t* offsets, uint32_t k,
                          uint64_t* fine_out, uint32_t* first_out);
 void set_local_kernel_attributes();
