@@ -268,14 +268,18 @@ k_local_big(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
 constexpr int kSmallThreads = 128;
 constexpr int kSmallItems = kSmallCap / kSmallThreads;  // 8
 static_assert(kSmallThreads * kSmallItems == (int)kSmallCap, "small class fits one CTA");
-static_assert(kLocalThreads * kLocalItems == kBucketCap, "medium class fits one CTA");
+// The medium class (1025..4096 keys): 512 threads of 8 slots, two CTAs per SM
+// (32 warps; 256 threads of 16 slots ran 16 warps at twice the registers).
+constexpr int kMediumThreads = 512;
+constexpr int kMediumItems = kBucketCap / kMediumThreads;  // 8
+static_assert(kMediumThreads * kMediumItems == kBucketCap, "medium class fits one CTA");
 
 }  // namespace
 
 void set_local_kernel_attributes() {
   cudaFuncSetAttribute(k_local_sort<kSmallThreads, kSmallItems, kClassSmall>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * kCtaSortBytesPerElem);
-  cudaFuncSetAttribute(k_local_sort<kLocalThreads, kLocalItems, kClassMedium>,
+  cudaFuncSetAttribute(k_local_sort<kMediumThreads, kMediumItems, kClassMedium>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * kCtaSortBytesPerElem);
   cudaFuncSetAttribute(k_local_quicksort<kLocalThreads, kBucketCap, kClassMedium>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs_smem_bytes(kBucketCap));
@@ -306,8 +310,8 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
           <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kBucketCap), e.stream>>>(
               st, items, item_cap, B, 0x9e3779b97f4a7c15ULL);
     else
-      k_local_sort<kLocalThreads, kLocalItems, kClassMedium>
-          <<<e.num_sms * 2, kLocalThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(
+      k_local_sort<kMediumThreads, kMediumItems, kClassMedium>
+          <<<e.num_sms * 2, kMediumThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(
               st, items, item_cap, B);
   }
   {
