@@ -300,7 +300,7 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *   serve_slots, serve_batch_keys, serve_alone_min  serving runtime (see
  *                rsort_submit); fixed once the runtime has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
- *                (64..4096, default 640).
+ *                (64..4096, default 1536).
  *   medium_sort  buckets of 1025..4096 keys: 0 (default) equal-width bins and
  *                rank-by-counting; 1 in-SM quicksort whose pivots are the
  *                binary-tree median approximation (see rsort_approx_median)

@@ -63,7 +63,7 @@ struct rsort_ctx {
   // 4096-key sub-tiles with 512 threads (longer runs per bucket)
   int wide_scatter_k = 1024;
   // tunable "target_bucket": automatic fan-outs aim at final buckets of this
-  // many keys (mostly below the 1024-key in-SM size class)
+  // many keys (mostly inside the 1025..2048-key in-SM size class)
   uint32_t target_bucket = rsort::kTargetBucket;
   // tunable "medium_sort": buckets of 1025..4096 keys are sorted by the
   // equal-width bins (0, default) or by quicksort with tree-median pivots (1)

@@ -10,6 +10,9 @@
 //   larger (only after the     merge sort through global memory by one CTA:
 //   last partition level)      bitonic-sorted runs, then pairwise merges
 //
+// The sorted buckets come in three size classes, each its own kernel with a
+// CTA shape that fits it: <= 1024 keys (128 threads, 10 CTAs per SM),
+// <= 2048 keys (256 threads, 5 per SM), <= 4096 keys (512 threads, 2 per SM).
 // Buckets are taken from a device work list with an atomic cursor by a
 // persistent grid.  The final store restores float64 bit patterns.
 #include "cta_quicksort.cuh"
@@ -161,9 +164,10 @@ __device__ __forceinline__ int64_t next_item(DevState* st, int cls, uint64_t cap
 // of 128 threads measured 17% faster than 6 at 2^28 keys).
 constexpr int kSmallPerSm = 10;
 
-// Buckets of up to NT*IT keys, sorted by one CTA each (cta_sort_pairs).
-template <int NT, int IT, int CLS>
-__global__ void __launch_bounds__(NT, (NT == 128 ? kSmallPerSm : 2))
+// Buckets of up to NT*IT keys, sorted by one CTA each (cta_sort_pairs),
+// MINB CTAs resident per SM.
+template <int NT, int IT, int CLS, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   constexpr int kCap = NT * IT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -268,7 +272,12 @@ k_local_big(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
 constexpr int kSmallThreads = 128;
 constexpr int kSmallItems = kSmallCap / kSmallThreads;  // 8
 static_assert(kSmallThreads * kSmallItems == (int)kSmallCap, "small class fits one CTA");
-// The medium class (1025..4096 keys): 512 threads of 8 slots, two CTAs per SM
+// The mid class (1025..2048 keys): 256 threads of 8 slots, 5 CTAs per SM.
+constexpr int kMidThreads = 256;
+constexpr int kMidItems = (int)kMidCap / kMidThreads;  // 8
+constexpr int kMidPerSm = 5;
+static_assert(kMidThreads * kMidItems == (int)kMidCap, "mid class fits one CTA");
+// The medium class (2049..4096 keys): 512 threads of 8 slots, two CTAs per SM
 // (32 warps; 256 threads of 16 slots ran 16 warps at twice the registers).
 constexpr int kMediumThreads = 512;
 constexpr int kMediumItems = kBucketCap / kMediumThreads;  // 8
@@ -277,9 +286,13 @@ static_assert(kMediumThreads * kMediumItems == kBucketCap, "medium class fits on
 }  // namespace
 
 void set_local_kernel_attributes() {
-  cudaFuncSetAttribute(k_local_sort<kSmallThreads, kSmallItems, kClassSmall>,
+  cudaFuncSetAttribute(k_local_sort<kSmallThreads, kSmallItems, kClassSmall, kSmallPerSm>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallCap * kCtaSortBytesPerElem);
-  cudaFuncSetAttribute(k_local_sort<kMediumThreads, kMediumItems, kClassMedium>,
+  cudaFuncSetAttribute(k_local_sort<kMidThreads, kMidItems, kClassMid, kMidPerSm>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidCap * kCtaSortBytesPerElem);
+  cudaFuncSetAttribute(k_local_quicksort<kLocalThreads, (int)kMidCap, kClassMid>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs_smem_bytes(kMidCap));
+  cudaFuncSetAttribute(k_local_sort<kMediumThreads, kMediumItems, kClassMedium, 2>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, kBucketCap * kCtaSortBytesPerElem);
   cudaFuncSetAttribute(k_local_quicksort<kLocalThreads, kBucketCap, kClassMedium>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qs_smem_bytes(kBucketCap));
@@ -300,8 +313,19 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   }
   {
     Scope sc(e, "local_sort");
-    k_local_sort<kSmallThreads, kSmallItems, kClassSmall>
+    k_local_sort<kSmallThreads, kSmallItems, kClassSmall, kSmallPerSm>
         <<<e.num_sms * kSmallPerSm, kSmallThreads, kSmallCap * kCtaSortBytesPerElem, e.stream>>>(st, items, item_cap, B);
+  }
+  {
+    Scope sc(e, "local_sort_mid");
+    if (e.medium_sort == 1)
+      k_local_quicksort<kLocalThreads, (int)kMidCap, kClassMid>
+          <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kMidCap), e.stream>>>(
+              st, items, item_cap, B, 0x243f6a8885a308d3ULL);
+    else
+      k_local_sort<kMidThreads, kMidItems, kClassMid, kMidPerSm>
+          <<<e.num_sms * kMidPerSm, kMidThreads, kMidCap * kCtaSortBytesPerElem, e.stream>>>(
+              st, items, item_cap, B);
   }
   {
     Scope sc(e, "local_sort_medium");
@@ -310,7 +334,7 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
           <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kBucketCap), e.stream>>>(
               st, items, item_cap, B, 0x9e3779b97f4a7c15ULL);
     else
-      k_local_sort<kMediumThreads, kMediumItems, kClassMedium>
+      k_local_sort<kMediumThreads, kMediumItems, kClassMedium, 2>
           <<<e.num_sms * 2, kMediumThreads, kBucketCap * kCtaSortBytesPerElem, e.stream>>>(
               st, items, item_cap, B);
   }

@@ -1642,10 +1642,10 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
                     scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096) <=
                         g_wide_scatter_smem_max;
   // Stored bucket ids spare the staged scatter its second classification.
-  // The warp-direct scatter classifies again, and so does the wide one: with
-  // 1024+ buckets its L2-resident write frontiers are the bottleneck, and the
-  // extra id stream measured slower there (4.04 vs 3.82 ms at 2^28 keys).
-  if (P.warp_direct || wide) src.bid = nullptr;
+  // The warp-direct scatter classifies again, and so does a level of 1024+
+  // buckets: there the L2-resident write frontiers are the bottleneck, and
+  // the extra id stream measured slower (4.04 vs 3.82 ms at 2^28 keys).
+  if (P.warp_direct || kmax_level >= 1024) src.bid = nullptr;
   {
     Scope sc(e, nm[4]);
     if (P.warp_direct)

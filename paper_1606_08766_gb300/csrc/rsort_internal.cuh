@@ -21,7 +21,7 @@ constexpr int kMaxK = 2048;                       // buckets per partition step
 constexpr int kMaxKDeep = 512;                    // buckets at levels >= 2
 constexpr int kMaxFine = 10240;                   // fine partitions of an overpartitioned step
 constexpr int kBucketCap = 4096;                  // T_s: largest bucket one CTA sorts
-constexpr int kTargetBucket = 640;                // aim for this final bucket size
+constexpr int kTargetBucket = 1536;               // aim for this final bucket size
                                                   // (mostly below the 1024-key class)
 constexpr int kSampleChunk = 8192;                // sample sort: pairs per CTA chunk
 constexpr int kSampleThreads = 512;               // sample sort CTA
@@ -37,9 +37,17 @@ enum : uint16_t { kWhereOut = 0, kWhereTmp = 1, kWhereInput = 2 };
 // How a final bucket is finished.
 enum : uint16_t { kKindSort = 0, kKindCopy = 1, kKindBig = 2 };
 // Work lists of the in-SM sort, one per size class (each has its own kernel):
-// copy-through, <= kSmallCap keys, <= kBucketCap keys, oversize.
-enum : int { kClassCopy = 0, kClassSmall = 1, kClassMedium = 2, kClassBig = 3, kNumClasses = 4 };
+// copy-through, <= kSmallCap keys, <= kMidCap keys, <= kBucketCap keys, oversize.
+enum : int {
+  kClassCopy = 0,
+  kClassSmall = 1,   // <= kSmallCap keys
+  kClassMid = 2,     // <= kMidCap keys
+  kClassMedium = 3,  // <= kBucketCap keys
+  kClassBig = 4,
+  kNumClasses = 5
+};
 constexpr uint32_t kSmallCap = 1024;
+constexpr uint32_t kMidCap = 2048;
 
 // A segment waiting to be partitioned (input of a level).
 struct SegIn {
@@ -80,8 +88,8 @@ struct FinalItem {
 // Device-resident control block of one call.
 struct DevState {
   uint32_t nseg[2];         // segment lists (ping-pong by level parity)
-  uint32_t nfinal_c[4];     // final items per size class
-  uint32_t cursor_c[4];     // work counters of the in-SM sort kernels
+  uint32_t nfinal_c[kNumClasses];  // final items per size class
+  uint32_t cursor_c[kNumClasses];  // work counters of the in-SM sort kernels
   uint32_t error;           // capacity / wait errors (bit flags)
   uint32_t max_bucket_l1;   // largest level-1 bucket
   uint32_t levels_used;
@@ -238,7 +246,8 @@ __device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint6
                                            const FinalItem& f, uint32_t err_flag) {
   const int cls = f.kind == kKindCopy ? kClassCopy
                   : f.kind == kKindBig ? kClassBig
-                  : (f.size <= kSmallCap ? kClassSmall : kClassMedium);
+                  : (f.size <= kSmallCap ? kClassSmall
+                                         : (f.size <= kMidCap ? kClassMid : kClassMedium));
   // one atomic per (warp, class): the lanes appending to the same list share it
   const uint32_t act = __activemask();
   const uint32_t peers = __match_any_sync(act, (uint32_t)cls);
