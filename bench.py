@@ -369,6 +369,37 @@ def serving_leg(dev, requests=2000, lo_log2=4, hi_log2=20, seed=5):
             "poisson_rate_requests_s": rate, "p50_us": poi["p50_us"], "p99_us": poi["p99_us"]}
 
 
+def instances_leg(ctx, dev, n=1 << 26, p=1024, reps=3):
+    """The full sort on every input instance (Section 6's robustness claim:
+    duplicates, skew and presorted orders should not slow the sort down).
+    Device time per sort (median of reps after one warm-up) and GKeys/s."""
+    import numpy as np
+    import torch
+
+    import instances
+
+    out = {"workload": f"rsort_sort of n=2^{n.bit_length() - 1} u64 keys, p={p}, per instance"}
+    stream = torch.cuda.current_stream(dev)
+    ko = torch.empty(n, dtype=torch.int64, device=dev)
+    po = torch.empty(n, dtype=torch.int32, device=dev)
+    for name in instances.NAMES:
+        keys = torch.from_numpy(instances.generate(name, n, p=p, seed=1).view(np.int64)).to(dev)
+        ctx.sort(keys, p=p, keys_out=ko, perm_out=po)
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.sort(keys, p=p, keys_out=ko, perm_out=po)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        ms = sorted(ts)[len(ts) // 2]
+        out[name] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9}
+        del keys
+    return out
+
+
 def partition_leg(ctx, dev, n=1 << 26, k=1024, over=10, reps=3):
     """The partition step alone on duplicate-heavy and unique inputs: the
     robust step, the NTB ablation (classification by key only) and AMS
@@ -496,32 +527,80 @@ def run_rsort(args):
             "algo_bytes_per_launch": kernels[dom]["algo_bytes"],
             "traffic": traffic * elems.get(dom.split(".")[0], n) if traffic else None}
 
-    # -- end-to-end through the C ABI with host buffers (pinned), copies timed
+    # -- end to end through the C ABI with host buffers (pinned): every step
+    # copies its input up and its result (keys + permutation) down, inside the
+    # timed region.  Serial: one stream, copy / sort / copy in turn.
+    # Pipelined: consecutive steps overlap on three streams (upload, sort,
+    # download) with two device buffer sets, as a streaming caller would run.
     keys_pin = torch.from_numpy(keys_h.view(np.int64)).pin_memory()
-    out_pin = torch.empty(n, dtype=torch.int64).pin_memory()
-    perm_pin = torch.empty(n, dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    outs_pin = [(torch.empty(n, dtype=torch.int64).pin_memory(),
+                 torch.empty(n, dtype=torch.int32).pin_memory()) for _ in range(2)]
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
+    serial_steps = max(1, min(args.steps, 3))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
+    for _ in range(serial_steps):
         keys.copy_(keys_pin, non_blocking=True)
         step()
-        out_pin.copy_(keys_out, non_blocking=True)
-        perm_pin.copy_(perm, non_blocking=True)
+        outs_pin[0][0].copy_(keys_out, non_blocking=True)
+        outs_pin[0][1].copy_(perm, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
-    e2e = {"value": (n * ws) / (e2e_ms / 1e3) / 1e9, "unit": METRIC,
-           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + n * 4}
+    serial_ms = max_over_ranks(e0.elapsed_time(e1) / serial_steps, dist, dev)
+
+    dev_in = [keys, torch.empty_like(keys)]
+    dev_out = [(keys_out, perm), (torch.empty_like(keys_out), torch.empty_like(perm))]
+    s_up, s_sort, s_down = (torch.cuda.Stream(dev), torch.cuda.Stream(dev),
+                            torch.cuda.Stream(dev))
+    up_done = [torch.cuda.Event() for _ in range(2)]
+    sort_done = [torch.cuda.Event() for _ in range(2)]
+    down_done = [torch.cuda.Event() for _ in range(2)]
+    pipe_steps = max(4, min(args.steps, 8))
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(s_up)
+    for i in range(pipe_steps):
+        j = i & 1
+        with torch.cuda.stream(s_up):
+            if i >= 2:
+                s_up.wait_event(sort_done[j])      # step i-2 has read dev_in[j]
+            dev_in[j].copy_(keys_pin, non_blocking=True)
+            up_done[j].record(s_up)
+        s_sort.wait_event(up_done[j])
+        if i >= 2:
+            s_sort.wait_event(down_done[j])        # dev_out[j] is downloaded
+        ctx.sort_raw(0, dev_in[j].data_ptr(), dev_out[j][0].data_ptr(),
+                     dev_out[j][1].data_ptr(), n, P_VIRTUAL, 1, s_sort.cuda_stream)
+        sort_done[j].record(s_sort)
+        with torch.cuda.stream(s_down):
+            s_down.wait_event(sort_done[j])
+            outs_pin[j][0].copy_(dev_out[j][0], non_blocking=True)
+            outs_pin[j][1].copy_(dev_out[j][1], non_blocking=True)
+            down_done[j].record(s_down)
+    s_down.wait_event(down_done[(pipe_steps - 2) & 1])
+    p1.record(s_down)
+    torch.cuda.synchronize(dev)
+    ctx.check()
+    pipe_ms = max_over_ranks(p0.elapsed_time(p1) / pipe_steps, dist, dev)
+    assert bool(torch.equal(outs_pin[0][0], outs_pin[1][0].clone())), "pipelined outputs differ"
+    e2e = {"value": (n * ws) / (pipe_ms / 1e3) / 1e9, "unit": METRIC,
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + n * 4,
+           "mode": "pipelined over 3 streams (upload / sort / download of consecutive steps overlap)",
+           "serial_value": (n * ws) / (serial_ms / 1e3) / 1e9, "steps": pipe_steps}
+    del dev_in, dev_out, outs_pin
 
     cpu = cpu_baseline_leg() if (rank == 0 and ws == 1) else None
     extra = {}
     if rank == 0 and ws == 1 and not args.skip_systems:
-        del keys_pin, out_pin, perm_pin
+        del keys_pin
+        torch.cuda.empty_cache()
+        extra["instances"] = instances_leg(ctx, dev)
         extra["partition_variants"] = partition_leg(ctx, dev)
         extra["batched"] = batched_leg(ctx, dev)
         torch.cuda.empty_cache()
