@@ -41,7 +41,9 @@ ALGO_BYTES_PER_KEY = {
     "L2.scatter": 24,       # read + write (key, position)
     "L3.classify": 8,
     "L3.scatter": 24,
-    "local_sort": 24,       # read + write (key, position)
+    "local_sort": 24,       # read + write (key, position), buckets <= 1024 keys
+    "local_sort_mid": 24,   # buckets of 1025..2048 keys
+    "local_sort_medium": 24,  # buckets of 2049..4096 keys
 }
 
 
@@ -50,11 +52,10 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    "L1.scatter": 34.13,   # 1.0713 GB read + 1.2191 GB write at 2^26 keys
-    "L2.scatter": 26.33,   # 1.0114 + 0.7558 GB
-    "local_sort": 22.70,   # 0.7879 + 0.7355 GB
-    "L1.classify": 8.07,   # 0.5374 + 0.0042 GB
-    "L2.classify": 9.69,   # 0.5718 + 0.0783 GB
+    "L1.scatter": 34.18,   # 1.0734 GB read + 1.2206 GB write at 2^26 keys
+    "L2.scatter": 25.29,   # 0.9671 + 0.7303 GB
+    "L1.classify": 8.06,   # 0.5370 + 0.0040 GB
+    "L2.classify": 9.39,   # 0.5519 + 0.0783 GB
 }
 
 
@@ -507,15 +508,17 @@ def run_rsort(args):
     _, _, st = ctx.sort(keys, p=P_VIRTUAL, seed=1, keys_out=keys_out, perm_out=perm, stats=True)
     torch.cuda.synchronize(dev)
     elems = {"L1": n, "L2": st.level_elems[1] if len(st.level_elems) > 1 else n,
-             "L3": st.level_elems[2] if len(st.level_elems) > 2 else 0, "local": n}
+             "L3": st.level_elems[2] if len(st.level_elems) > 2 else 0,
+             "local_copy": st.class_elems[0], "local_sort": st.class_elems[1],
+             "local_sort_mid": st.class_elems[2], "local_sort_medium": st.class_elems[3],
+             "local_big": st.class_elems[4]}
     peak, peak_kind = _peaks()
     kernels = {}
     for name, (ms, cnt) in phases.items():
         per = ms / max(cnt, 1)
         info = {"ms_per_launch": per, "launches": cnt, "share": ms / max(ms_total, 1e-9)}
         if name in ALGO_BYTES_PER_KEY:
-            lvl = name.split(".")[0] if "." in name else "local"
-            units = elems.get(lvl, n)
+            units = elems.get(name.split(".")[0] if "." in name else name, n)
             info["algo_bytes"] = ALGO_BYTES_PER_KEY[name] * units
             info["gbs"] = info["algo_bytes"] / (per / 1e3) / 1e9
         kernels[name] = info
@@ -525,7 +528,8 @@ def run_rsort(args):
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak,
             "unit": "GB/s", "frac": kernels[dom]["gbs"] / peak, "peak_kind": peak_kind,
             "algo_bytes_per_launch": kernels[dom]["algo_bytes"],
-            "traffic": traffic * elems.get(dom.split(".")[0], n) if traffic else None}
+            "traffic": (traffic * elems.get(dom.split(".")[0] if "." in dom else dom, n)
+                        if traffic else None)}
 
     # -- end to end through the C ABI with host buffers (pinned): every step
     # copies its input up and its result (keys + permutation) down, inside the

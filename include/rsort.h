@@ -64,6 +64,8 @@ typedef struct {
     uint64_t final_buckets;  /* buckets handed to the in-SM sort                 */
     uint64_t bytes_moved;    /* algorithmic HBM bytes of the whole call          */
     uint64_t level_elems[4]; /* elements partitioned at levels 1..4 (0: unused)  */
+    uint64_t class_elems[5]; /* elements handed to the in-SM sort by size class:
+                                copy-through, <= 1024, <= 2048, <= 4096, larger */
 } rsort_stats;
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the scratch

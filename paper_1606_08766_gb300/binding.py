@@ -34,7 +34,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("p", ctypes.c_uint32), ("levels", ctypes.c_uint32),
                 ("path", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
                 ("max_over_mean", ctypes.c_double), ("final_buckets", ctypes.c_uint64),
-                ("bytes_moved", ctypes.c_uint64), ("level_elems", ctypes.c_uint64 * 4)]
+                ("bytes_moved", ctypes.c_uint64), ("level_elems", ctypes.c_uint64 * 4),
+                ("class_elems", ctypes.c_uint64 * 5)]
 
 
 class _PartOpts(ctypes.Structure):
@@ -68,6 +69,7 @@ class Stats:
     final_buckets: int
     bytes_moved: int
     level_elems: list
+    class_elems: list
 
 
 def library_path() -> str:
@@ -214,7 +216,7 @@ class Context:
         if stats:
             return keys_out, perm_out, Stats(st.n, st.p, st.levels, st.path, st.max_bucket,
                                              st.max_over_mean, st.final_buckets, st.bytes_moved,
-                                             list(st.level_elems))
+                                             list(st.level_elems), list(st.class_elems))
         return keys_out, perm_out
 
     def sort_raw(self, key_type: int, d_in: int, d_out: int, d_perm: int, n: int, p: int,

@@ -240,6 +240,7 @@ __global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uin
   for (int c = 0; c < kNumClasses; ++c) {
     st->nfinal_c[c] = 0;
     st->cursor_c[c] = 0;
+    st->class_elems[c] = 0;
   }
   st->error = 0;
   st->max_bucket_l1 = 0;

@@ -729,6 +729,8 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
       bytes += (i == 0 ? 28ull : 32ull) * h.level_elems[i];
     }
     opt_stats->bytes_moved = bytes;
+    static_assert(kNumClasses == 5, "rsort_stats.class_elems has one entry per size class");
+    for (int i = 0; i < kNumClasses; ++i) opt_stats->class_elems[i] = h.class_elems[i];
     if (h.error) return latch(c, RSORT_EDEVICE);
   }
   return RSORT_OK;

@@ -90,6 +90,7 @@ struct DevState {
   uint32_t nseg[2];         // segment lists (ping-pong by level parity)
   uint32_t nfinal_c[kNumClasses];  // final items per size class
   uint32_t cursor_c[kNumClasses];  // work counters of the in-SM sort kernels
+  uint64_t class_elems[kNumClasses];  // elements handed to each size class
   uint32_t error;           // capacity / wait errors (bit flags)
   uint32_t max_bucket_l1;   // largest level-1 bucket
   uint32_t levels_used;
@@ -254,7 +255,11 @@ __device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint6
   const int leader = __ffs(peers) - 1;
   const int lane = threadIdx.x & 31;
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&st->nfinal_c[cls], (uint32_t)__popc(peers));
+  const uint32_t keys = __reduce_add_sync(peers, f.size);
+  if (lane == leader) {
+    base = atomicAdd(&st->nfinal_c[cls], (uint32_t)__popc(peers));
+    atomicAdd((unsigned long long*)&st->class_elems[cls], (unsigned long long)keys);
+  }
   base = __shfl_sync(peers, base, leader);
   uint32_t lt;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));

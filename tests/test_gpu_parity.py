@@ -134,6 +134,12 @@ def test_seed_invariance_and_stats(ctx):
     b, pb, sb = ctx.sort(keys, p=64, seed=12345, stats=True)
     assert torch.equal(a, b) and torch.equal(pa, pb)
     assert sa.p == 64 and sa.levels >= 1 and sa.max_over_mean < 1.5
+    # every element reaches exactly one in-SM size class
+    for st in (sa, sb):
+        assert sum(st.class_elems) == keys.numel()
+    u = _dev(instances.generate("uniform", (1 << 20) + 3, p=64, seed=2))
+    _, _, su = ctx.sort(u, p=64, stats=True)
+    assert sum(su.class_elems) == u.numel() and su.class_elems[4] == 0
 
 
 def test_invalid_arguments(ctx):
