@@ -11,16 +11,18 @@
 // are as even as possible) done implicitly by the median of the pairs.
 //
 // Segments are kept on a shared-memory stack; the smaller side is handled
-// first, so the stack depth stays below log2 of the size.  Segments of at most
-// kQsSmall elements are finished by rank-by-counting.
+// first, so the stack depth stays below log2 of the size.  A segment of at
+// most kQsBase elements is finished by the bins sort of cta_sort.cuh, as the
+// paper's quicksort hands small inputs to a local sort.
 #pragma once
 
+#include "cta_sort.cuh"
 #include "rsort_internal.cuh"
 #include "tree_median.cuh"
 
 namespace rsort {
 
-constexpr int kQsSmall = 64;       // segments up to this size: rank-by-counting
+constexpr int kQsBase = 1024;      // segments up to this size: the bins sort
 constexpr int kQsSample = 256;     // pivot sample (tree leaves) per segment
 constexpr int kQsWindow = 16;      // window size k of the median tree
 constexpr int kQsStack = 64;       // segment stack entries
@@ -39,11 +41,14 @@ struct QsSmem {
   uint8_t* tn1;
   uint8_t* tr1;
   uint32_t* stack;  // [2 * kQsStack]
+  CtaSortSmem base; // the bins sort of segments of at most kQsBase elements
 };
 
-// Shared memory of a QsSmem for `cap` elements.
+// Shared memory of a QsSmem for `cap` elements, followed by the CtaSortSmem
+// of the base case (kQsBase elements).
 __host__ __device__ constexpr size_t qs_smem_bytes(size_t cap) {
-  return cap * 24 + (size_t)kQsSample * 24 + (size_t)kQsSample * 2 + (size_t)kQsStack * 8;
+  return cap * 24 + (size_t)kQsSample * 24 + (size_t)kQsSample * 2 + (size_t)kQsStack * 8 +
+         (size_t)kQsBase * kCtaSortBytesPerElem;
 }
 
 __device__ inline QsSmem qs_carve(unsigned char* base, uint32_t cap) {
@@ -61,7 +66,10 @@ __device__ inline QsSmem qs_carve(unsigned char* base, uint32_t cap) {
   q.tn0 = p; p += kQsSample / 2;
   q.tr0 = p; p += kQsSample / 2;
   q.tn1 = p; p += kQsSample / 2;
-  q.tr1 = p;
+  q.tr1 = p; p += kQsSample / 2;
+  q.base.k = (uint64_t*)p; p += (size_t)kQsBase * 8;
+  q.base.i = (uint32_t*)p; p += (size_t)kQsBase * 4;
+  q.base.hist = (uint32_t*)p;
   return q;
 }
 
@@ -69,7 +77,9 @@ __device__ inline QsSmem qs_carve(unsigned char* base, uint32_t cap) {
 // tree's coins (it changes the pivots, never the result).
 template <int NT>
 __device__ void cta_quicksort_pairs(const QsSmem& q, uint32_t m, uint64_t seed,
-                                    uint64_t* scan_sm) {
+                                    uint64_t* scan_sm, uint64_t* red) {
+  static_assert(kQsBase % NT == 0, "the base case holds kQsBase / NT elements per thread");
+  constexpr int kBaseItems = kQsBase / NT;
   __shared__ uint32_t s_top;
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
@@ -85,19 +95,23 @@ __device__ void cta_quicksort_pairs(const QsSmem& q, uint32_t m, uint64_t seed,
     const uint32_t len = hi - lo;
     __syncthreads();
     if (tid == 0) s_top = top;
-    if (len <= (uint32_t)kQsSmall) {
-      // rank-by-counting inside the segment
-      uint64_t k = 0;
-      uint32_t i = 0, rank = 0;
-      if (tid < len) {
-        k = q.ak[lo + tid];
-        i = q.ai[lo + tid];
-        for (uint32_t t = 0; t < len; ++t) rank += pair_less(q.ak[lo + t], q.ai[lo + t], k, i) ? 1u : 0u;
+    if (len <= (uint32_t)kQsBase) {
+      // base case: the bins sort (rank-by-counting when tiny); the segment's
+      // elements are in no particular order
+      uint64_t key[kBaseItems];
+      uint32_t idx[kBaseItems];
+#pragma unroll
+      for (int r = 0; r < kBaseItems; ++r) {
+        const uint32_t e = r * NT + tid;
+        if (e < len) {
+          key[r] = q.ak[lo + e];
+          idx[r] = q.ai[lo + e];
+        }
       }
-      __syncthreads();
-      if (tid < len) {
-        q.ak[lo + rank] = k;
-        q.ai[lo + rank] = i;
+      cta_sort_pairs<NT, kBaseItems>(key, idx, len, false, q.base, red, scan_sm);
+      for (uint32_t t = tid; t < len; t += NT) {
+        q.ak[lo + t] = q.base.k[t];
+        q.ai[lo + t] = q.base.i[t];
       }
       __syncthreads();
       continue;

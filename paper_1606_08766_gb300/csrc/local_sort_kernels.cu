@@ -209,11 +209,12 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
 // segment (cta_quicksort.cuh).  The result is the same; the bins of
 // cta_sort_pairs measured faster, so this is an alternative, not the default.
 template <int NT, int CAP, int CLS>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, 1)
 k_local_quicksort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QsSmem q = qs_carve(smem_raw, CAP);
   __shared__ uint64_t scan_sm[NT / 32];
+  __shared__ uint64_t red[2 * NT / 32];
   __shared__ uint32_t s_item;
   const FinalItem* list = items + (uint64_t)CLS * cap;
   for (;;) {
@@ -228,7 +229,7 @@ k_local_quicksort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B, ui
       q.ai[t] = i;
     }
     __syncthreads();
-    cta_quicksort_pairs<NT>(q, f.size, splitmix64_at(seed, (uint64_t)it), scan_sm);
+    cta_quicksort_pairs<NT>(q, f.size, splitmix64_at(seed, (uint64_t)it), scan_sm, red);
     for (uint32_t t = threadIdx.x; t < f.size; t += NT) store_out(B, f.start + t, q.ak[t], q.ai[t]);
     __syncthreads();
   }
