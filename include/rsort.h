@@ -303,6 +303,11 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                rsort_submit); fixed once the runtime has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
  *                (64..4096, default 1536).
+ *   max_levels   partition levels of rsort_sort / rsort_segmented before
+ *                every bucket is final (1..3, default 3).  A bucket still
+ *                above 4096 keys after the last level is merge-sorted
+ *                through global memory by one CTA (slow; with 3 levels the
+ *                sampling makes it vanishingly rare below 2^31 keys).
  *   medium_sort  buckets of 1025..4096 keys: 0 (default) equal-width bins and
  *                rank-by-counting; 1 in-SM quicksort whose pivots are the
  *                binary-tree median approximation (see rsort_approx_median)

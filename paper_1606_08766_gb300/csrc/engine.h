@@ -68,6 +68,10 @@ struct rsort_ctx {
   // tunable "medium_sort": buckets of 1025..4096 keys are sorted by the
   // equal-width bins (0, default) or by quicksort with tree-median pivots (1)
   int medium_sort = 0;
+  // tunable "max_levels": partition levels before every bucket is final
+  // (1..3, default 3); buckets still above one SM's capacity after the last
+  // level are merge-sorted through global memory by one CTA each
+  int max_levels = rsort::kMaxLevels;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

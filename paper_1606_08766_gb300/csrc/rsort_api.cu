@@ -295,6 +295,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->target_bucket = (uint32_t)v;
     return RSORT_OK;
   }
+  if (strcmp(name, "max_levels") == 0) {
+    if (v < 1 || v > kMaxLevels) return RSORT_EINVAL;
+    c->max_levels = (int)v;
+    return RSORT_OK;
+  }
   if (strcmp(name, "medium_sort") == 0) {
     if (v != 0 && v != 1) return RSORT_EINVAL;
     c->medium_sort = (int)v;
@@ -384,7 +389,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
     p.need_tmp = false;
     p.levels = 0;
   } else {
-    plan_levels(p, n, k1, 1, c->num_sms, kMaxLevels);
+    plan_levels(p, n, k1, 1, c->num_sms, c->max_levels);
     p.need_tmp = true;
   }
   layout(p);
@@ -398,7 +403,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
-  plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, kMaxLevels);
+  plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, c->max_levels);
   p.final_cap += num_segments;
   p.need_tmp = true;
   layout(p);
@@ -822,6 +827,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "target_bucket") == 0) {
     *value = c->target_bucket;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "max_levels") == 0) {
+    *value = c->max_levels;
     return RSORT_OK;
   }
   if (strcmp(name, "medium_sort") == 0) {

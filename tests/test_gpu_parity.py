@@ -196,6 +196,21 @@ def test_full_size_2p28(ctx, name):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("name", instances.NAMES)
+def test_every_instance_2p24(ctx, name):
+    # every input instance at the fan-out of 1024 virtual PEs, checked
+    # through the properties that fix the output
+    n = 1 << 24
+    keys = instances.generate(name, n, p=1024, seed=2)
+    t = _dev(keys)
+    ko, po, st = ctx.sort(t, p=1024, seed=3, stats=True)
+    torch.cuda.synchronize()
+    _check_sorted_permutation(t, ko, po)
+    assert sum(st.class_elems) == n
+    ctx.check()
+    del t, ko, po
+
+
 CONFIGS = {
     "tree_staged": {"classifier": 0, "warp_direct_max_k": 0},
     "tree_warpdirect": {"classifier": 0, "warp_direct_max_k": 2048},
