@@ -30,12 +30,19 @@ static_assert(kRankMax <= kLocalThreads, "rank-by-counting holds one element per
 struct CtaSortSmem {
   uint64_t* k;     // [cap]      cap = NT * ITEMS
   uint32_t* i;     // [cap]
-  uint32_t* hist;  // [cap + cap/2]  2*cap 16-bit bin counters packed in pairs,
-                   //                then the list of bins holding several elements
+  uint32_t* hist;  // [cap + cap/4 + cap/2]  up to 2*cap 16-bit bin counters
+                   //   packed in pairs (one pad word after every thread's run
+                   //   of counter words), then the list of bins holding
+                   //   several elements
 };
 
 // Shared memory per element of capacity that a CtaSortSmem needs.
-constexpr int kCtaSortBytesPerElem = 8 + 4 + 4 + 2;
+constexpr int kCtaSortBytesPerElem = 8 + 4 + 4 + 1 + 2;
+
+// Counter word w of a scan in which every thread owns 2^lp consecutive words
+// sits at w + (w >> lp): each thread's run starts one bank further on, so the
+// lanes of a warp walking their runs in step hit distinct banks.
+__device__ __forceinline__ uint32_t padded_word(uint32_t w, int lp) { return w + (w >> lp); }
 
 template <int NT>
 __device__ __forceinline__ void block_minmax_u64(uint64_t& mn, uint64_t& mx, uint64_t* red) {
@@ -62,8 +69,8 @@ __device__ __forceinline__ void block_minmax_u64(uint64_t& mn, uint64_t& mx, uin
   __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t bin_start(const uint32_t* hist, uint32_t b) {
-  return (hist[b >> 1] >> ((b & 1) << 4)) & 0xffffu;
+__device__ __forceinline__ uint32_t bin_start(const uint32_t* hist, uint32_t b, int lp) {
+  return (hist[padded_word(b >> 1, lp)] >> ((b & 1) << 4)) & 0xffffu;
 }
 
 // Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
@@ -73,6 +80,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
                                bool in_position_order, const CtaSortSmem& s, uint64_t* red,
                                uint64_t* scan_sm) {
   constexpr uint32_t kCap = NT * ITEMS;
+  static_assert(ITEMS >= 4, "the padded counters need cap/4 >= NT words of slack");
   const uint32_t tid = threadIdx.x;
   if (m <= (uint32_t)kRankMax) {
 #pragma unroll
@@ -114,7 +122,11 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   const uint64_t range = mx - mn;
   const int bits = range ? 64 - __clzll((long long)range) : 0;
   const int shift = bits > lognb ? bits - lognb : 0;
-  for (uint32_t w = tid; w < nb / 2; w += NT) s.hist[w] = 0;
+  // counter words, each thread's run of them, and the padded layout
+  const uint32_t words = nb / 2;
+  const uint32_t per = (words + NT - 1) / NT;  // a power of two
+  const int lp = log2_u32(per);
+  for (uint32_t w = tid; w < words + (words >> lp); w += NT) s.hist[w] = 0;
   __shared__ uint32_t s_nmulti;
   if (tid == 0) s_nmulti = 0;
   __syncthreads();
@@ -124,21 +136,19 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     if (r * NT + tid < m) {
       const uint32_t b = (uint32_t)((key[r] - mn) >> shift);
       const uint32_t sh = (b & 1) << 4;
-      const uint32_t old = atomicAdd(&s.hist[b >> 1], 1u << sh);
+      const uint32_t old = atomicAdd(&s.hist[padded_word(b >> 1, lp)], 1u << sh);
       bs[r] = (b << 16) | ((old >> sh) & 0xffffu);
     }
   }
   __syncthreads();
   // exclusive scan of the nb 16-bit counters (nb/2 words; each thread a run),
   // which also finds out whether any bin is crowded
-  const uint32_t words = nb / 2;
-  const uint32_t per = (words + NT - 1) / NT;
   const uint32_t w0 = tid * per;
   bool crowd = false;
   {
     uint32_t loc = 0;
     for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
-      const uint32_t v = s.hist[w];
+      const uint32_t v = s.hist[padded_word(w, lp)];
       const uint32_t a = v & 0xffffu, b = v >> 16;
       loc += a + b;
       crowd |= a > (uint32_t)kBinLimit || b > (uint32_t)kBinLimit;
@@ -146,9 +156,10 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     uint64_t tot;
     uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
     for (uint32_t w = w0; w < w0 + per && w < words; ++w) {
-      const uint32_t v = s.hist[w];
+      const uint32_t pw = padded_word(w, lp);
+      const uint32_t v = s.hist[pw];
       const uint32_t lo = run, hi = run + (v & 0xffffu);
-      s.hist[w] = lo | (hi << 16);
+      s.hist[pw] = lo | (hi << 16);
       run = hi + (v >> 16);
     }
   }
@@ -166,12 +177,12 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   }
   // counting-sort scatter into the bins; the second element to land in a bin
   // puts the bin on the list of bins that still need ordering
-  uint32_t* multi = s.hist + kCap;
+  uint32_t* multi = s.hist + kCap + kCap / 4;
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     if (r * NT + tid < m) {
       const uint32_t b = bs[r] >> 16, o = bs[r] & 0xffffu;
-      const uint32_t p = bin_start(s.hist, b) + o;
+      const uint32_t p = bin_start(s.hist, b, lp) + o;
       s.k[p] = key[r];
       s.i[p] = idx[r];
       if (o == 1) multi[atomicAdd(&s_nmulti, 1u)] = b;
@@ -183,8 +194,8 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   const uint32_t nmulti = s_nmulti;
   for (uint32_t j = tid; j < nmulti; j += NT) {
     const uint32_t b = multi[j];
-    const uint32_t lo = bin_start(s.hist, b);
-    const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1) : m;
+    const uint32_t lo = bin_start(s.hist, b, lp);
+    const uint32_t hi = b + 1 < nb ? bin_start(s.hist, b + 1, lp) : m;
     uint64_t* bk = s.k + lo;
     uint32_t* bi = s.i + lo;
     for (uint32_t a = 1; a < hi - lo; ++a) {
