@@ -303,6 +303,12 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                rsort_submit); fixed once the runtime has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
  *                (64..4096, default 1536).
+ *   deep_levels_stable  1: the partition levels of rsort_sort /
+ *                rsort_segmented after the first keep input order inside
+ *                buckets; 0 (default): they rank elements by shared-memory
+ *                atomics.  The result is the same (the in-SM sort orders
+ *                (key, position) pairs); level 1 and rsort_partition always
+ *                keep input order.
  *   max_levels   partition levels of rsort_sort / rsort_segmented before
  *                every bucket is final (1..3, default 3).  A bucket still
  *                above 4096 keys after the last level is merge-sorted

@@ -17,7 +17,8 @@
 //   (> kBinLimit)       Sort"), which needs no assumption on the keys
 //
 // A bucket whose keys are all equal and whose elements arrive in position
-// order (every bucket produced by the stable scatter) is already sorted.
+// order (every bucket produced by the stable scatter) is already sorted; if
+// they arrive in another order, the bins are taken over the positions.
 #pragma once
 
 #include "rsort_internal.cuh"
@@ -73,11 +74,22 @@ __device__ __forceinline__ uint32_t bin_start(const uint32_t* hist, uint32_t b, 
   return (hist[padded_word(b >> 1, lp)] >> ((b & 1) << 4)) & 0xffffu;
 }
 
+// After a sort in which the positions stood in for keys that were all equal
+// to key_all: writes that key back into the sorted slots.
+template <int NT>
+__device__ __forceinline__ void restore_common_key(const CtaSortSmem& s, uint32_t m, int by_pos,
+                                                   uint64_t key_all) {
+  if (!by_pos) return;
+  for (uint32_t t = threadIdx.x; t < m; t += NT) s.k[t] = key_all;
+  __syncthreads();
+}
+
 // Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
-// in_position_order: the elements arrive with increasing positions.
-template <int NT, int ITEMS>
+// in_position_order() says whether the elements arrive with increasing
+// positions; it is asked only when all keys are equal.
+template <int NT, int ITEMS, typename InOrderFn>
 __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], uint32_t m,
-                               bool in_position_order, const CtaSortSmem& s, uint64_t* red,
+                               InOrderFn in_position_order, const CtaSortSmem& s, uint64_t* red,
                                uint64_t* scan_sm) {
   constexpr uint32_t kCap = NT * ITEMS;
   static_assert(ITEMS >= 4, "the padded counters need cap/4 >= NT words of slack");
@@ -107,7 +119,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
   }
   block_minmax_u64<NT>(mn, mx, red);
-  if (mn == mx && in_position_order) {
+  if (mn == mx && in_position_order()) {
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const uint32_t e = r * NT + tid;
@@ -115,6 +127,28 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
     __syncthreads();
     return;
+  }
+  // all keys equal, in no particular order: (key, position) order is the
+  // order of the positions, so the positions (distinct) stand in for the
+  // keys below and the common key is put back at the end
+  __shared__ uint64_t s_key_all;
+  __shared__ int s_by_pos;
+  if (tid == 0) {
+    s_by_pos = mn == mx;
+    s_key_all = mn;
+  }
+  if (mn == mx) {
+    mn = ~0ULL;
+    mx = 0;
+#pragma unroll
+    for (int r = 0; r < ITEMS; ++r) {
+      if (r * NT + tid < m) {
+        key[r] = idx[r];
+        mn = key[r] < mn ? key[r] : mn;
+        mx = key[r] > mx ? key[r] : mx;
+      }
+    }
+    block_minmax_u64<NT>(mn, mx, red);
   }
   // equal-width bins over [mn, mx]
   const uint32_t nb = 2 * next_pow2_u32(m);  // <= 2 * kCap
@@ -173,6 +207,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
     for (uint32_t e = m + tid; e < P; e += NT) { s.k[e] = ~0ULL; s.i[e] = ~0u; }
     block_bitonic_sort<NT>(s.k, s.i, (int)P);
+    restore_common_key<NT>(s, m, s_by_pos, s_key_all);
     return;
   }
   // counting-sort scatter into the bins; the second element to land in a bin
@@ -212,6 +247,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
   }
   __syncthreads();
+  restore_common_key<NT>(s, m, s_by_pos, s_key_all);
   (void)kCap;
 }
 

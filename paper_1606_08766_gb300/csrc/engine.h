@@ -72,6 +72,10 @@ struct rsort_ctx {
   // (1..3, default 3); buckets still above one SM's capacity after the last
   // level are merge-sorted through global memory by one CTA each
   int max_levels = rsort::kMaxLevels;
+  // tunable "deep_levels_stable": the sort's levels after the first keep
+  // input order inside buckets (1) or rank by shared-memory atomics (0,
+  // default); level 1, the partition step, always keeps it
+  int deep_levels_stable = 0;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

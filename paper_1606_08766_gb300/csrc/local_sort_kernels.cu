@@ -2,8 +2,8 @@
 // bucket size as the paper chooses its algorithm by input size (Section 6,
 // "four algorithms cover the entire range"; Appendix "Parameter Tuning"):
 //
-//   size 1 or equality bucket  copy through (the stable scatter already left
-//                              the elements in position order)
+//   size 1 or equality bucket  copy through (a stable scatter already left
+//   of a stable level          the elements in position order)
 //   size <= kBucketCap         cta_sort_pairs (cta_sort.cuh): rank-by-counting
 //                              for tiny buckets, equal-width bins + rank-by-
 //                              counting for the rest, bitonic when keys cluster
@@ -188,7 +188,8 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
     load_bucket<NT, IT>(B, f, key, idx);
   }
   while (it >= 0) {
-    cta_sort_pairs<NT, IT>(key, idx, f.size, true, s, red, scan_sm);
+    cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
+                           red, scan_sm);
     // claim and start loading the next bucket before this one is stored, so
     // its loads are in flight while the stores go out
     const int64_t it2 = next_item(st, CLS, cap, &s_item);

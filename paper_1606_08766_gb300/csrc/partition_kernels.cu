@@ -401,10 +401,12 @@ k_sample(const DevState* st, const LevelSeg* segs, Src src, uint64_t* samp_key,
 
 // Step 2a: sort chunks of up to kSampleChunk sample pairs in one CTA each
 // (cta_sort_pairs).  Single-chunk samples go straight to the sorted-sample
-// array.  Samples of a segment are drawn in position order.
+// array.  Samples are drawn in segment order, which is position order when
+// the segment's level input is (in_order).
 __global__ void __launch_bounds__(kSampleThreads, 1)
 k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_key,
-                     uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx) {
+                     uint32_t* samp_idx, uint64_t* ssamp_key, uint32_t* ssamp_idx,
+                     int in_order) {
   constexpr int NT = kSampleThreads, IT = kSampleChunk / kSampleThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CtaSortSmem s;
@@ -431,7 +433,7 @@ k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_ke
         idx[r] = samp_idx[base + e];
       }
     }
-    cta_sort_pairs<NT, IT>(key, idx, len, true, s, red, scan_sm);
+    cta_sort_pairs<NT, IT>(key, idx, len, [&] { return in_order != 0; }, s, red, scan_sm);
     uint64_t* ok = sg.nschunks == 1 ? ssamp_key : samp_key;
     uint32_t* oi = sg.nschunks == 1 ? ssamp_idx : samp_idx;
     for (uint32_t t = threadIdx.x; t < len; t += NT) {
@@ -577,27 +579,31 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
 static size_t g_wide_scatter_smem_max = 0;
 
 // Shared memory of the staged scatter with NW warps and ST-key sub-tiles.
-__host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, int nw, int st) {
+// The stable scatter keeps per-warp counters and winner slots per bucket; the
+// unstable one a single 32-bit counter per bucket (in place of the former).
+__host__ __device__ inline size_t scatter_smem_bytes(uint32_t kmax, int mode, int nw, int st,
+                                                     bool stable = true) {
   size_t b = part_common_bytes(kmax, mode);
   b += (size_t)(kmax + 1) * 4 + 4;
-  b += (size_t)nw * cnt_stride(kmax) * 2;
+  b += stable ? (size_t)nw * cnt_stride(kmax) * 2 : (size_t)kmax * 4;
   b += (size_t)kmax * 4;
-  b += (size_t)nw * kmax;
+  b += stable ? (size_t)nw * kmax : 0;
   b = (b + 15) & ~(size_t)15;
   return b + 2 * ((size_t)st * (8 + 4 + 2) + 16);
 }
 
-__device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int mode, int nw) {
+__device__ inline PartSmem carve_scatter(unsigned char* base, uint32_t kmax, int mode, int nw,
+                                         bool stable = true) {
   PartSmem s = carve(base, kmax, false, mode);
   unsigned char* p = base + part_common_bytes(kmax, mode);
   s.sbase = (uint32_t*)p;
   p += (size_t)(kmax + 1) * 4 + 4;
   s.wcnt = (uint16_t*)p;
-  p += (size_t)nw * cnt_stride(kmax) * 2;
+  p += stable ? (size_t)nw * cnt_stride(kmax) * 2 : (size_t)kmax * 4;
   s.dlt = (uint32_t*)p;
   p += (size_t)kmax * 4;
   s.wwin = (uint8_t*)p;
-  p += (size_t)nw * kmax;
+  p += stable ? (size_t)nw * kmax : 0;
   s.buf = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
   return s;
 }
@@ -746,15 +752,20 @@ k_scan_down(const DevState* st, uint32_t* a, const uint32_t* sums) {
   }
 }
 
-// Step 5c: stable scatter.  Every chunk streams through two kST-key sub-tile
-// buffers (cp.async: sub-tile s+1 loads while s is processed).  Warp w owns
-// kSItems*32 consecutive elements of a sub-tile; an element's rank among the
-// earlier elements of its bucket in the sub-tile comes from warp-synchronous
-// match counting (warp order, then lane order = input order).  The sub-tile is
-// then counting-sorted by bucket into its own buffer and every bucket's run is
-// written out contiguously (write-combining through shared memory), so
-// buckets keep input order.
-template <int NT, int ST>
+// Step 5c: scatter.  Every chunk streams through two ST-key sub-tile buffers
+// (cp.async: sub-tile s+1 loads while s is processed).  Every element gets a
+// rank among the elements of its bucket in the sub-tile; the sub-tile is then
+// counting-sorted by bucket into its own buffer and every bucket's run is
+// written out contiguously (write-combining through shared memory).
+//   STABLE   warp w owns IT*32 consecutive elements; ranks come from
+//            warp-synchronous peer counting (warp order, then lane order =
+//            input order), so buckets keep input order -- the layout of the
+//            partition step.
+//   unstable one shared-memory atomic per element on its bucket's counter:
+//            buckets come out in no particular order, which a full sort's
+//            deeper levels may do (the in-SM sort orders (key, position)
+//            pairs).
+template <int NT, int ST, bool STABLE>
 __global__ void __launch_bounds__(NT, (NT <= 256 ? 2 : 1))
 k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
           const uint32_t* ssi, const uint32_t* hist_scan, Dst dst, uint32_t W, uint32_t kmax,
@@ -766,7 +777,11 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
   // position, one before the sub-tile when it starts at an odd one)
   constexpr size_t BUFB = (size_t)ST * (8 + 4 + 2) + 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PartSmem sm = carve_scatter(smem_raw, kmax, mode, NW);
+  PartSmem sm = carve_scatter(smem_raw, kmax, mode, NW, STABLE);
+  uint32_t* cntu = reinterpret_cast<uint32_t*>(sm.wcnt);  // unstable: one counter per bucket
+  if constexpr (!STABLE) {
+    for (uint32_t b = threadIdx.x; b < kmax; b += NT) cntu[b] = 0;
+  }
   __shared__ uint64_t scan_sm[NW];
   // sub-tile buffer i: keys, positions, bucket ids (addressed arithmetically so
   // that no descriptor array lives in local memory)
@@ -859,6 +874,14 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       } else {
         classify_batch<IT>(key, bk, [&](int r) { return idx[r]; }, sm.sp);
       }
+      if constexpr (!STABLE) {
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+          const bool v = q0 + r * 32 < len;
+          bk[r] = v ? bk[r] : 0xffffffffu;
+          lrank[r] = v ? atomicAdd(&cntu[bk[r]], 1u) : 0u;
+        }
+      } else {
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
 #pragma unroll
@@ -893,6 +916,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         __syncwarp();
         lrank[r] = c0 + __popc(peers & ltmask);
       }
+      }  // STABLE
       __syncthreads();
       {  // per bucket (each thread a run of buckets): exclusive prefix over the
          // warps' counts, in place; an exclusive scan of the bucket totals then
@@ -904,11 +928,16 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         uint32_t loc = 0;
         for (uint32_t b = bb0; b < bb1; ++b) {
           uint32_t tot = 0;
+          if constexpr (STABLE) {
 #pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
-            sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
-            tot += cnt;
+            for (int w = 0; w < NW; ++w) {
+              const uint32_t cnt = sm.wcnt[(size_t)w * kst + b];
+              sm.wcnt[(size_t)w * kst + b] = (uint16_t)tot;
+              tot += cnt;
+            }
+          } else {
+            tot = cntu[b];
+            cntu[b] = 0;  // ready for the next sub-tile (its atomics follow barriers)
           }
           sm.sbase[b] = tot;
           loc += tot;
@@ -929,7 +958,7 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
       for (int r = 0; r < IT; ++r) {
         const uint32_t b = bk[r];
         if (b != 0xffffffffu) {
-          const uint32_t q = sm.sbase[b] + my_cnt[b] + lrank[r];
+          const uint32_t q = sm.sbase[b] + (STABLE ? (uint32_t)my_cnt[b] : 0u) + lrank[r];
           B.key[q] = key[r];
           B.idx[q] = idx[r];
           B.b[q] = (uint16_t)b;
@@ -1161,10 +1190,12 @@ k_scatter_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* 
 }
 
 // Collect the buckets of the level: bucket sizes follow from the scanned
-// histogram.  Buckets that fit one SM, equality buckets (both bounding
-// splitters share one key, so every element has that key and the stable
-// scatter already left them in position order) and empty ones are final;
-// the rest become segments of the next level.
+// histogram.  Buckets that fit one SM, equality buckets of a stable level
+// (both bounding splitters share one key, so every element has that key and
+// the stable scatter already left them in position order) and empty ones are
+// final; the rest become segments of the next level.  After an unstable
+// scatter an equality bucket is a bucket like any other, and its elements
+// arrive at the in-SM sort in no particular order.
 __global__ void __launch_bounds__(256)
 k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_t* hist_scan,
           SegIn* list_out, int par_out, FinalItem* items, LevelParams P, uint16_t where,
@@ -1188,7 +1219,7 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
     if (P.level == 1) atomicMax(&st->max_bucket_l1, size);
     if (!emit_final || size == 0) continue;
     bool eq = false;
-    if (b >= 1 && b + 1 < sg.k) {
+    if (P.stable && b >= 1 && b + 1 < sg.k) {
       const uint64_t klo = ssk[sg.samp_off + ((uint64_t)b * sg.S) / sg.k];
       const uint64_t khi = ssk[sg.samp_off + ((uint64_t)(b + 1) * sg.S) / sg.k];
       eq = klo == khi;
@@ -1199,7 +1230,10 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
       it.idx_base = 0;
       it.size = size;
       it.where = where;
-      it.kind = (eq || size == 1) ? kKindCopy : (size <= kBucketCap ? kKindSort : kKindBig);
+      it.kind = (eq || size == 1)      ? kKindCopy
+                : size > kBucketCap    ? kKindBig
+                : P.stable             ? kKindSort
+                                       : kKindSortAny;
       if (it.kind == kKindBig) atomicAdd((unsigned long long*)&st->big_items, 1ull);
       push_final(st, items, P.final_cap, it, kErrFinalCap);
     } else {
@@ -1470,19 +1504,28 @@ void set_partition_kernel_attributes() {
                        (int)umax64(classify_smem_bytes(kMaxKDeep, 0, kCStagesDeep),
                                    classify_smem_bytes(kMaxKDeep, 1, kCStagesDeep)));
   (void)s;
-  cudaFuncSetAttribute(k_scatter<kPartThreads, 2048>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_scatter<kPartThreads, 2048, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)umax64(scatter_smem_bytes(kMaxK, 0, kPartWarps, 2048),
                                    scatter_smem_bytes(kMaxK, 1, kPartWarps, 2048)));
+  cudaFuncSetAttribute(k_scatter<kPartThreads, 2048, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)umax64(scatter_smem_bytes(kMaxK, 0, kPartWarps, 2048, false),
+                                   scatter_smem_bytes(kMaxK, 1, kPartWarps, 2048, false)));
   {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
     size_t limit = 0;
-    if (cudaFuncGetAttributes(&fa, k_scatter<512, 4096>) == cudaSuccess &&
+    if (cudaFuncGetAttributes(&fa, k_scatter<512, 4096, true>) == cudaSuccess &&
         (size_t)optin > fa.sharedSizeBytes) {
       limit = (size_t)optin - fa.sharedSizeBytes;
-      if (cudaFuncSetAttribute(k_scatter<512, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      if (cudaFuncSetAttribute(k_scatter<512, 4096, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)limit) != cudaSuccess ||
+          cudaFuncSetAttribute(k_scatter<512, 4096, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)limit) != cudaSuccess)
         limit = 0;
     }
@@ -1509,13 +1552,17 @@ int wd_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
 }
 
 // Resident CTAs per SM of the classify / scatter kernels for a bucket bound.
-int part_blocks_per_sm(uint32_t kmax, bool scatter, int mode) {
+int part_blocks_per_sm(uint32_t kmax, bool scatter, int mode, bool stable = true) {
   int nb = 0;
   const size_t smem = part_smem_bytes(kmax, scatter, mode);
-  if (scatter)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<kPartThreads, 2048>,
+  if (scatter && stable)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<kPartThreads, 2048, true>,
                                                   kPartThreads,
                                                   scatter_smem_bytes(kmax, mode, kPartWarps, 2048));
+  else if (scatter)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, k_scatter<kPartThreads, 2048, false>, kPartThreads,
+        scatter_smem_bytes(kmax, mode, kPartWarps, 2048, false));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_count<kCStages>, kPartThreads,
                                                   smem);
@@ -1529,10 +1576,14 @@ int classify_deep_blocks_per_sm(uint32_t kmax, int mode) {
   return nb > 0 ? nb : 1;
 }
 
-int wide_scatter_blocks_per_sm(uint32_t kmax, int mode) {
+int wide_scatter_blocks_per_sm(uint32_t kmax, int mode, bool stable) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<512, 4096>, 512,
-                                                scatter_smem_bytes(kmax, mode, 16, 4096));
+  if (stable)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<512, 4096, true>, 512,
+                                                  scatter_smem_bytes(kmax, mode, 16, 4096));
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter<512, 4096, false>, 512,
+                                                  scatter_smem_bytes(kmax, mode, 16, 4096, false));
   return nb > 0 ? nb : 1;
 }
 
@@ -1614,7 +1665,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
     Scope sc(e, nm[2]);
     const int smem = kSampleChunk * kCtaSortBytesPerElem;
     k_sample_sort_chunks<<<grid_for(P.schunk_cap, 1, sms), kSampleThreads, smem, e.stream>>>(
-        st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx);
+        st, segs, samp_key, samp_idx, ssamp_key, ssamp_idx, P.in_order);
   }
   {
     Scope sc(e, nm[3]);
@@ -1632,15 +1683,16 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       P.chunk_cap, 1,
       sms * (deep_c ? classify_deep_blocks_per_sm((uint32_t)kmax_level, mode)
                     : part_blocks_per_sm((uint32_t)kmax_level, false, mode)));
-  const int grid_s =
-      grid_for(P.chunk_cap, 1, sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode));
+  const bool stable = P.stable != 0;
+  const int grid_s = grid_for(P.chunk_cap, 1,
+                              sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode, stable));
   const size_t smem_wd = wd_smem_bytes((uint32_t)kmax_level, mode);
   const int grid_wd_c =
       grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, false, mode));
   const int grid_wd_s =
       grid_for(P.chunk_cap, 1, sms * wd_blocks_per_sm((uint32_t)kmax_level, true, mode));
   const bool wide = !P.warp_direct && kmax_level >= P.wide_scatter_k &&
-                    scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096) <=
+                    scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096, stable) <=
                         g_wide_scatter_smem_max;
   // Stored bucket ids spare the staged scatter its second classification.
   // The warp-direct scatter classifies again, and so does a level of 1024+
@@ -1678,15 +1730,29 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       k_scatter_wd<<<grid_wd_s, kPartThreads, smem_wd, e.stream>>>(
           st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level, unmap_out,
           mode);
+    else if (wide && stable)
+      k_scatter<512, 4096, true>
+          <<<grid_for(P.chunk_cap, 1,
+                      sms * wide_scatter_blocks_per_sm((uint32_t)kmax_level, mode, true)),
+             512, scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096), e.stream>>>(
+              st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level,
+              unmap_out, mode);
     else if (wide)
-      k_scatter<512, 4096><<<grid_for(P.chunk_cap, 1,
-                                      sms * wide_scatter_blocks_per_sm((uint32_t)kmax_level, mode)),
-                             512, scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096),
-                             e.stream>>>(st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W,
-                                         (uint32_t)kmax_level, unmap_out, mode);
-    else
-      k_scatter<kPartThreads, 2048>
+      k_scatter<512, 4096, false>
+          <<<grid_for(P.chunk_cap, 1,
+                      sms * wide_scatter_blocks_per_sm((uint32_t)kmax_level, mode, false)),
+             512, scatter_smem_bytes((uint32_t)kmax_level, mode, 16, 4096, false), e.stream>>>(
+              st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W, (uint32_t)kmax_level,
+              unmap_out, mode);
+    else if (stable)
+      k_scatter<kPartThreads, 2048, true>
           <<<grid_s, kPartThreads, scatter_smem_bytes((uint32_t)kmax_level, mode, kPartWarps, 2048),
+             e.stream>>>(st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W,
+                         (uint32_t)kmax_level, unmap_out, mode);
+    else
+      k_scatter<kPartThreads, 2048, false>
+          <<<grid_s, kPartThreads,
+             scatter_smem_bytes((uint32_t)kmax_level, mode, kPartWarps, 2048, false),
              e.stream>>>(st, segs, src, ssamp_key, ssamp_idx, hist, dst, P.W,
                          (uint32_t)kmax_level, unmap_out, mode);
   }

@@ -254,6 +254,10 @@ void enqueue_levels_and_local(rsort_ctx* c, Workspace& ws, const Plan& p, const 
   for (int L = 1; L <= p.levels; ++L) {
     const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
     LevelParams P = level_params(p, L, seed, kmax);
+    // level 1 keeps input order inside buckets; deeper levels may not (the
+    // in-SM sort orders (key, position) pairs either way)
+    P.stable = L == 1 ? 1 : c->deep_levels_stable;
+    P.in_order = L == 1 ? 1 : (L == 2 ? 1 : c->deep_levels_stable);
     Src src;
     if (L == 1) {
       src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
@@ -293,6 +297,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   if (strcmp(name, "target_bucket") == 0) {
     if (v < 64 || v > kBucketCap) return RSORT_EINVAL;
     c->target_bucket = (uint32_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "deep_levels_stable") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->deep_levels_stable = (int)v;
     return RSORT_OK;
   }
   if (strcmp(name, "max_levels") == 0) {
@@ -827,6 +836,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "target_bucket") == 0) {
     *value = c->target_bucket;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "deep_levels_stable") == 0) {
+    *value = c->deep_levels_stable;
     return RSORT_OK;
   }
   if (strcmp(name, "max_levels") == 0) {

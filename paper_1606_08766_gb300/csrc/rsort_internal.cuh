@@ -35,7 +35,11 @@ constexpr int kScanTile = 4096;                   // device scan tile (1024 x 4)
 // Where the elements of a final bucket live.
 enum : uint16_t { kWhereOut = 0, kWhereTmp = 1, kWhereInput = 2 };
 // How a final bucket is finished.
-enum : uint16_t { kKindSort = 0, kKindCopy = 1, kKindBig = 2 };
+//   kKindSort     sort in one CTA; its elements arrive in position order
+//   kKindCopy     already ordered (size 1, or an equality bucket of a stable level)
+//   kKindBig      larger than one CTA sorts (after the last level)
+//   kKindSortAny  sort in one CTA; its elements arrive in no particular order
+enum : uint16_t { kKindSort = 0, kKindCopy = 1, kKindBig = 2, kKindSortAny = 3 };
 // Work lists of the in-SM sort, one per size class (each has its own kernel):
 // copy-through, <= kSmallCap keys, <= kMidCap keys, <= kBucketCap keys, oversize.
 enum : int {
@@ -127,6 +131,12 @@ struct LevelParams {
   int wide_scatter_k;     // levels with at least this many buckets scatter 4096-key sub-tiles
   uint32_t target_bucket; // automatic fan-out aims at buckets of this many keys
   int no_tie_break = 0;   // 1: classify by key only (the NTB ablation)
+  int stable = 1;         // 1: buckets keep input order (the partition step's
+                          // layout); 0: a full sort's deeper level, ranked by
+                          // shared-memory atomics (the in-SM sort orders
+                          // (key, position) pairs, so the result is the same)
+  int in_order = 1;       // 1: the level's segments hold their elements in
+                          // position order (level 1, or after a stable level)
 };
 
 // AMS-sort overpartitioning of a one-segment partition step: b*k fine

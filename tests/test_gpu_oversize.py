@@ -133,3 +133,31 @@ def test_max_levels_invalid():
                 c.set_tunable("max_levels", v)
             assert e.value.status == EINVAL
         assert c.get_tunable("max_levels") == 3
+        assert c.get_tunable("deep_levels_stable") == 0
+        for v in (2, -1):
+            with pytest.raises(RsortError) as e:
+                c.set_tunable("deep_levels_stable", v)
+            assert e.value.status == EINVAL
+
+
+@pytest.mark.parametrize("stable", [0, 1])
+@pytest.mark.parametrize("name", ["zero", "deter_dupl", "rand_dupl", "uniform"])
+def test_third_level_after_unordered_level(oracle_mod, name, stable):
+    # 4096-key targets leave many level-2 buckets above 4096 keys, so a third
+    # level partitions them.  With deep_levels_stable = 0 the level-2 scatter
+    # ranks by atomics: level 3 then samples segments that are not in
+    # position order (all-equal ones included), and equality buckets are
+    # sorted by position instead of copied.
+    c = _ctx(3, target=4096)
+    try:
+        c.set_tunable("deep_levels_stable", stable)
+        n = (1 << 22) + 19
+        x = instances.generate(name, n, p=64, seed=8)
+        ko, po, st = c.sort(_dev(x), p=64, seed=4, stats=True)
+        _eq(ko, po, *oracle_mod.sort(x))
+        assert sum(st.class_elems) == n
+        if name != "zero":
+            assert st.levels == 3
+        c.check()
+    finally:
+        c.close()
