@@ -926,7 +926,26 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
         const uint32_t bb0 = threadIdx.x * per;
         const uint32_t bb1 = bb0 + per < k ? bb0 + per : k;
         uint32_t loc = 0;
-        for (uint32_t b = bb0; b < bb1; ++b) {
+        uint32_t b0s = bb0;
+        if constexpr (STABLE) {
+          // two buckets at a time: their 16-bit counters share a 32-bit word
+          // (rows have even length, bb0 is even when per is), and no count or
+          // prefix exceeds the sub-tile, so halfword adds never carry
+          for (; (per & 1) == 0 && b0s + 1 < bb1; b0s += 2) {
+            uint32_t tot2 = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+              uint32_t* cw = reinterpret_cast<uint32_t*>(sm.wcnt + (size_t)w * kst + b0s);
+              const uint32_t cnt2 = *cw;
+              *cw = tot2;
+              tot2 = __vadd2(tot2, cnt2);
+            }
+            sm.sbase[b0s] = tot2 & 0xffffu;
+            sm.sbase[b0s + 1] = tot2 >> 16;
+            loc += (tot2 & 0xffffu) + (tot2 >> 16);
+          }
+        }
+        for (uint32_t b = b0s; b < bb1; ++b) {
           uint32_t tot = 0;
           if constexpr (STABLE) {
 #pragma unroll
