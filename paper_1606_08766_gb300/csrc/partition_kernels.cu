@@ -77,6 +77,7 @@ struct Splitters {
   uint32_t* tbl;    // [2^tbits] packed (first, end) splitter of a bin (table mode)
   uint64_t* key;    // [k-1]  sorted splitter keys
   uint32_t* idx;    // [k-1]  their positions (tie-breakers)
+  uint16_t* rend;   // [k-1]  end of the run of splitters whose key equals key[j]
   uint64_t lo, hi;  // smallest / largest splitter key
   int logK;         // log2(Kp)
   int tbits;        // table bits
@@ -104,6 +105,17 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
     sp.idx[j] = ssi[sg.samp_off + r];
   }
   __syncthreads();
+  // end of every run of equal splitter keys (keys are sorted, so the run of
+  // key[j] is contiguous); tie-breaks search positions inside the run only
+  for (uint32_t j = threadIdx.x; j < sp.nspl; j += NT) {
+    const uint64_t kj = sp.key[j];
+    uint32_t lo = j + 1, hi = sp.nspl;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (sp.key[mid] == kj) lo = mid + 1; else hi = mid;
+    }
+    sp.rend[j] = (uint16_t)lo;
+  }
   if (sp.mode == 0) {
     for (uint32_t i = threadIdx.x + 1; i < Kp; i += NT) {
       const int d = 31 - __clz(i);
@@ -146,12 +158,48 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
 // node where it turned left, which is the bounding splitter's key; only if x
 // equals it is the search repeated on the run of equal splitter keys with
 // positions as tie-breakers (pos_of(r) is evaluated only then).
+//
+// The splitters whose key is x are [bb, rend[bb]), in increasing position;
+// the bucket is bb plus the number of them placed before position i.  A long
+// run (many copies of one key) holds positions of a stratified sample, close
+// to evenly spaced: the search starts at an interpolated guess and gallops
+// to a bracket around the answer, a few steps instead of log2 of the run.
 __device__ __forceinline__ uint32_t tie_break(uint32_t bb, uint64_t x, uint32_t i,
                                               const Splitters& sp) {
-  uint32_t lo = bb, hi = sp.nspl;
+  (void)x;
+  uint32_t lo = bb, hi = sp.rend[bb];
+  if (hi - lo > 8) {
+    const uint32_t p0 = sp.idx[lo], p1 = sp.idx[hi - 1];
+    if (i <= p0) return lo;
+    if (i > p1) return hi;
+    // now idx[lo] < i <= idx[hi - 1]: the answer is in (lo, hi - 1]
+    const float f = __fdividef((float)(i - p0) * (float)(hi - 1 - lo), (float)(p1 - p0));
+    uint32_t g = lo + (uint32_t)f;
+    g = g < lo + 1 ? lo + 1 : (g > hi - 1 ? hi - 1 : g);
+    uint32_t a, b;  // idx[a] < i <= idx[b]
+    if (sp.idx[g] < i) {
+      a = g;
+      uint32_t d = 1;
+      while (a + d < hi - 1 && sp.idx[a + d] < i) {
+        a += d;
+        d <<= 1;
+      }
+      b = a + d < hi - 1 ? a + d : hi - 1;
+    } else {
+      b = g;
+      uint32_t d = 1;
+      while (b - lo > d && sp.idx[b - d] >= i) {
+        b -= d;
+        d <<= 1;
+      }
+      a = b - lo > d ? b - d : lo;
+    }
+    lo = a + 1;
+    hi = b;
+  }
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (sp.key[mid] == x && sp.idx[mid] < i) lo = mid + 1; else hi = mid;
+    if (sp.idx[mid] < i) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
@@ -519,7 +567,7 @@ constexpr size_t kSBufBytes = (size_t)kST * (8 + 4 + 2);
 __host__ __device__ inline size_t part_common_bytes(uint32_t kmax, int mode) {
   const size_t Kp = next_pow2_u32(kmax);
   size_t b = (mode & 1) == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
-  b += (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 4;
+  b += (size_t)kmax * 8 + (size_t)kmax * 4 + (size_t)kmax * 2 + (size_t)kmax * 4;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -558,6 +606,7 @@ __device__ inline PartSmem carve(unsigned char* base, uint32_t kmax, bool scatte
   s.sp.key = (uint64_t*)p; p += (size_t)kmax * 8;
   s.sp.idx = (uint32_t*)p; p += (size_t)kmax * 4;
   s.hist = (uint32_t*)p; p += (size_t)kmax * 4;
+  s.sp.rend = (uint16_t*)p; p += (size_t)kmax * 2;
   p = base + part_common_bytes(kmax, mode);
   s.sbase = nullptr;
   s.wcnt = nullptr;
@@ -1286,7 +1335,7 @@ constexpr int kGreedyThreads = 1024;
 
 __host__ __device__ inline size_t fine_smem_bytes(uint32_t K) {
   const uint32_t Kp = next_pow2_u32(K);
-  return ((size_t)4 << table_bits_for(Kp)) + (size_t)K * (8 + 4 + 4);
+  return ((size_t)4 << table_bits_for(Kp)) + (size_t)K * (8 + 4 + 4 + 2);
 }
 
 __host__ __device__ inline size_t greedy_smem_bytes(uint32_t K, uint32_t k) {
@@ -1314,6 +1363,8 @@ k_fine_count(const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t*
   sp.idx = (uint32_t*)p;
   p += (size_t)K * 4;
   uint32_t* cnt = (uint32_t*)p;
+  p += (size_t)K * 4;
+  sp.rend = (uint16_t*)p;
   load_splitters<kFineThreads>(sg, ssk, ssi, sp);
   for (uint32_t b = threadIdx.x; b < K; b += kFineThreads) cnt[b] = 0;
   __syncthreads();

@@ -54,6 +54,38 @@ def test_partition_matches_oracle(ctx, oracle_mod, name, k):
     ctx.check()
 
 
+def _clustered_ties(n: int, seed: int) -> np.ndarray:
+    """Distinct random keys, except for two keys copied over unevenly spaced
+    positions: dense blocks, a sparse stride and a lone tail.  The tied
+    splitters' positions are then far from evenly spaced."""
+    rng = np.random.default_rng(seed)
+    x = rng.integers(1 << 20, 2**64, n, dtype=np.uint64)
+    x[: n // 5] = 7
+    x[n // 2: n // 2 + n // 50] = 7
+    x[n // 5: n // 2: 97] = 7
+    x[n - n // 40:] = 7
+    x[3 * n // 5: 3 * n // 5 + n // 8] = 11
+    x[3 * n // 5 + n // 8::13] = 11
+    return x
+
+
+@pytest.mark.parametrize("k", [16, 200, 1024])
+def test_partition_clustered_ties(ctx, oracle_mod, k):
+    n = (1 << 18) + 77
+    keys = _clustered_ties(n, k)
+    for seed in (1, 2):
+        ref = oracle_mod.partition(keys, k, seed=seed)
+        ko, po, off = ctx.partition(_dev(keys), k, seed=seed)
+        np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+        np.testing.assert_array_equal(_host_u32(po), ref["pos_out"])
+        np.testing.assert_array_equal(_host_u64(ko), ref["keys_out"])
+    rk, rp = oracle_mod.sort(keys)
+    ko, po = ctx.sort(_dev(keys), p=k)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+    ctx.check()
+
+
 def test_partition_f64_matches_oracle(ctx, oracle_mod):
     keys, _ = instances.segmented_f64(1, 17, seed=3)
     keys = keys[: 100_000]
