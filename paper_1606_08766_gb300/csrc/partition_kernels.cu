@@ -253,6 +253,17 @@ __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uin
       uint32_t lo = pr[r] & 0xffffu, hi = pr[r] >> 16;
       const uint32_t end = hi;
       uint64_t ub = ~0ULL;
+      // the bin's first splitter may already bound x (always so when a run of
+      // copies of x fills the bin): then no search is needed
+      if (lo < hi) {
+        const uint64_t k0 = sp.key[lo];
+        if (k0 >= x[r]) {
+          hi = lo;
+          ub = k0;
+        } else {
+          ++lo;
+        }
+      }
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         const uint64_t km = sp.key[mid];
