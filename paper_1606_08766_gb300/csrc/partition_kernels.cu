@@ -1350,7 +1350,7 @@ __host__ __device__ inline size_t fine_smem_bytes(uint32_t K) {
 }
 
 __host__ __device__ inline size_t greedy_smem_bytes(uint32_t K, uint32_t k) {
-  return (size_t)(K + 1) * 8 + (size_t)(k + 1) * 4;
+  return (size_t)(K + 1) * 4 + (size_t)(k + 1) * 4;
 }
 
 __global__ void __launch_bounds__(kFineThreads, 1)
@@ -1405,28 +1405,50 @@ k_fine_count(const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t*
 
 // End of the greedy group that starts at fine partition j0: the largest
 // j in (j0, K] with P[j] - P[j0] <= L (P: prefix sums, every size <= L).
-__device__ __forceinline__ uint32_t greedy_next(const uint64_t* P, uint32_t K, uint32_t j0,
-                                                uint64_t L) {
-  const uint64_t base = P[j0];
-  uint32_t lo = j0 + 1, step = 1;
-  while (lo + step <= K && P[lo + step] - base <= L) {
-    lo += step;
-    step *= 2;
+__device__ __forceinline__ uint32_t greedy_next(const uint32_t* P, uint32_t K, uint32_t j0,
+                                                uint64_t L, uint32_t guess) {
+  // the group starting at fine partition j0 ends after the last j with
+  // P[j] - P[j0] <= L (it takes at least one partition); prefix sums are
+  // below 2^32, so the target saturates there
+  const uint64_t t64 = (uint64_t)P[j0] + L;
+  const uint32_t target = t64 > 0xffffffffull ? 0xffffffffu : (uint32_t)t64;
+  const uint32_t first = j0 + 1;
+  if (first >= K || P[first] > target) return first;
+  // answer in [first, K]: start at the guess and gallop to a bracket a < b
+  // with P[a] <= target < P[b] (b = K + 1 stands for "past the end")
+  uint32_t g = j0 + guess;
+  g = g < first ? first : (g > K ? K : g);
+  uint32_t a, b;
+  if (P[g] <= target) {
+    a = g;
+    uint32_t d = 1;
+    while (a + d <= K && P[a + d] <= target) {
+      a += d;
+      d <<= 1;
+    }
+    b = a + d <= K ? a + d : K + 1;
+  } else {
+    b = g;
+    uint32_t d = 1;
+    while (b - first > d && P[b - d] > target) {
+      b -= d;
+      d <<= 1;
+    }
+    a = b - first > d ? b - d : first;
   }
-  uint32_t hi = lo + step <= K ? lo + step - 1 : K;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (P[mid] - base <= L) lo = mid; else hi = mid - 1;
+  while (b - a > 1) {
+    const uint32_t mid = (a + b) >> 1;
+    if (P[mid] <= target) a = mid; else b = mid;
   }
-  return lo;
+  return a;
 }
 
 // Groups the greedy scan opens under bound L (stops counting past kmax).
-__device__ __forceinline__ uint32_t greedy_count(const uint64_t* P, uint32_t K, uint64_t L,
-                                                 uint32_t kmax) {
+__device__ __forceinline__ uint32_t greedy_count(const uint32_t* P, uint32_t K, uint64_t L,
+                                                 uint32_t kmax, uint32_t guess) {
   uint32_t g = 0, j = 0;
   while (j < K && g <= kmax) {
-    j = greedy_next(P, K, j, L);
+    j = greedy_next(P, K, j, L, guess);
     ++g;
   }
   return g == 0 ? 1 : g;
@@ -1439,8 +1461,9 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
   __shared__ uint32_t s_best;
   const LevelSeg sg = segs[0];
   const uint32_t k = sg.k, K = k * op.over;
-  uint64_t* P = (uint64_t*)smem_raw;                 // [K + 1]
-  uint32_t* first = (uint32_t*)(P + K + 1);          // [k + 1]
+  uint32_t* P = (uint32_t*)smem_raw;                 // [K + 1] (sums below 2^32)
+  uint32_t* first = P + K + 1;                       // [k + 1]
+  const uint32_t guess = op.over;                    // fine partitions per group on average
   const uint32_t tid = threadIdx.x;
   // prefix sums of the fine sizes, one run of fine partitions per thread
   const uint32_t per = (K + kGreedyThreads - 1) / kGreedyThreads;
@@ -1457,7 +1480,7 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
   if (tid == 0) P[0] = 0;
   for (uint32_t j = j0; j < j1; ++j) {
     run += op.fine_cnt[j];
-    P[j + 1] = run;
+    P[j + 1] = (uint32_t)run;
   }
   // largest fine size (max-reduce through the scan scratch)
 #pragma unroll
@@ -1480,7 +1503,7 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
     const uint64_t L = lo + (span * (tid + 1)) / kGreedyThreads;
     if (tid == 0) s_best = kGreedyThreads;
     __syncthreads();
-    if (greedy_count(P, K, L, k) <= k) atomicMin(&s_best, tid);
+    if (greedy_count(P, K, L, k, guess) <= k) atomicMin(&s_best, tid);
     __syncthreads();
     const uint32_t t = s_best;  // t <= kGreedyThreads - 1: L(last) = hi is feasible
     const uint64_t nhi = lo + (span * (t + 1)) / kGreedyThreads;
@@ -1493,7 +1516,7 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
     uint32_t g = 0, j = 0;
     while (j < K && g < k) {
       first[g++] = j;
-      j = greedy_next(P, K, j, lo);
+      j = greedy_next(P, K, j, lo, guess);
     }
     if (g == 0) first[g++] = 0;
     for (; g <= k; ++g) first[g] = K;
