@@ -1334,11 +1334,12 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
 //   k_fine_count    exact sizes of the K = b*k fine partitions of the same
 //                   sample (fine splitter j = sorted sample floor(j*S/K)),
 //                   counted per CTA in shared memory
-//   k_group_greedy  one CTA: the smallest load bound L for which the in-order
-//                   greedy scan needs at most k groups (a 1024-way search per
-//                   round), then that scan; the k-1 group boundaries are
-//                   written after the sample as the splitters of the ordinary
-//                   k-way step, and the segment is pointed at them
+//   k_group_*       the smallest load bound L for which the in-order greedy
+//                   scan needs at most k groups (candidate bounds checked by
+//                   every thread of the GPU per round), then that scan; the
+//                   k-1 group boundaries are written after the sample as the
+//                   splitters of the ordinary k-way step, and the segment is
+//                   pointed at them
 // ---------------------------------------------------------------------------
 constexpr int kFineThreads = 512;
 constexpr int kFineItems = 8;
@@ -1350,7 +1351,7 @@ __host__ __device__ inline size_t fine_smem_bytes(uint32_t K) {
 }
 
 __host__ __device__ inline size_t greedy_smem_bytes(uint32_t K, uint32_t k) {
-  return (size_t)(K + 1) * 4 + (size_t)(k + 1) * 4;
+  return (size_t)(K + 1) * 4 + (size_t)(k + 1) * 4 + (size_t)K * 2;
 }
 
 __global__ void __launch_bounds__(kFineThreads, 1)
@@ -1454,16 +1455,24 @@ __device__ __forceinline__ uint32_t greedy_count(const uint32_t* P, uint32_t K, 
   return g == 0 ? 1 : g;
 }
 
+// The greedy's bound L is searched by the whole GPU.  k_group_prep (one CTA)
+// writes the prefix sums P of the fine sizes and the first bracket
+// [lo, hi] (hi always feasible); every k_group_search launch spreads
+// gridDim candidate bounds over the bracket, one per CTA, each checked by a
+// greedy scan over P in shared memory; k_group_narrow keeps the sub-bracket
+// below the smallest feasible candidate.  Four rounds of 3 CTAs per SM narrow
+// any bracket below 2^33 to one value, the smallest feasible bound;
+// k_group_finish (one CTA) runs the greedy scan with it.
+// search[0] = lo, search[1] = hi, search[2] = smallest feasible candidate index.
+constexpr int kSearchThreads = 256;
+constexpr int kSearchRounds = 4;
+
 __global__ void __launch_bounds__(kGreedyThreads, 1)
-k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+k_group_prep(const LevelSeg* segs, Overpart op) {
   __shared__ uint64_t scan_sm[kGreedyThreads / 32];
-  __shared__ uint32_t s_best;
   const LevelSeg sg = segs[0];
   const uint32_t k = sg.k, K = k * op.over;
-  uint32_t* P = (uint32_t*)smem_raw;                 // [K + 1] (sums below 2^32)
-  uint32_t* first = P + K + 1;                       // [k + 1]
-  const uint32_t guess = op.over;                    // fine partitions per group on average
+  uint32_t* P = op.prefix;
   const uint32_t tid = threadIdx.x;
   // prefix sums of the fine sizes, one run of fine partitions per thread
   const uint32_t per = (K + kGreedyThreads - 1) / kGreedyThreads;
@@ -1480,7 +1489,7 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
   if (tid == 0) P[0] = 0;
   for (uint32_t j = j0; j < j1; ++j) {
     run += op.fine_cnt[j];
-    P[j + 1] = (uint32_t)run;
+    P[j + 1] = (uint32_t)run;  // sums below 2^32
   }
   // largest fine size (max-reduce through the scan scratch)
 #pragma unroll
@@ -1490,33 +1499,79 @@ k_group_greedy(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
   }
   if ((tid & 31) == 0) scan_sm[tid >> 5] = mx;
   __syncthreads();
-  uint64_t maxc = 0;
-  for (int w = 0; w < kGreedyThreads / 32; ++w) maxc = scan_sm[w] > maxc ? scan_sm[w] : maxc;
-  __syncthreads();
-  // bound: every group holds at least ceil(n/k) in the worst case and at least
-  // the largest fine partition; ceil(n/k) + maxc always needs at most k groups
-  const uint64_t avg = (n + k - 1) / k;
-  uint64_t lo = avg > maxc ? avg : maxc;
-  uint64_t hi = avg + maxc > lo ? avg + maxc : lo;
-  while (lo < hi) {
-    const uint64_t span = hi - lo;
-    const uint64_t L = lo + (span * (tid + 1)) / kGreedyThreads;
-    if (tid == 0) s_best = kGreedyThreads;
-    __syncthreads();
-    if (greedy_count(P, K, L, k, guess) <= k) atomicMin(&s_best, tid);
-    __syncthreads();
-    const uint32_t t = s_best;  // t <= kGreedyThreads - 1: L(last) = hi is feasible
-    const uint64_t nhi = lo + (span * (t + 1)) / kGreedyThreads;
-    const uint64_t nlo = t == 0 ? lo : lo + (span * t) / kGreedyThreads + 1;
-    __syncthreads();
-    lo = nlo;
-    hi = nhi;
+  if (tid == 0) {
+    uint64_t maxc = 0;
+    for (int w = 0; w < kGreedyThreads / 32; ++w) maxc = scan_sm[w] > maxc ? scan_sm[w] : maxc;
+    // every group holds at least ceil(n/k) in the worst case and at least the
+    // largest fine partition; ceil(n/k) + maxc always needs at most k groups
+    const uint64_t avg = (n + k - 1) / k;
+    const uint64_t lo = avg > maxc ? avg : maxc;
+    op.search[0] = lo;
+    op.search[1] = avg + maxc > lo ? avg + maxc : lo;
+    op.search[2] = ~0ull;
   }
+}
+
+__global__ void __launch_bounds__(kSearchThreads)
+k_group_search(const LevelSeg* segs, Overpart op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint64_t lo = op.search[0], hi = op.search[1];
+  if (lo >= hi) return;  // settled (the same for every CTA of this launch)
+  const uint32_t k = segs[0].k, K = k * op.over;
+  uint32_t* P = (uint32_t*)smem_raw;   // [K + 1]
+  uint16_t* nxt = (uint16_t*)(P + K + 1);  // [K]
+  for (uint32_t j = threadIdx.x; j <= K; j += kSearchThreads) P[j] = op.prefix[j];
+  __syncthreads();
+  // this CTA's candidate bound (the last CTA's is hi): the end of the group
+  // that would start at every fine partition, in parallel, then one thread
+  // counts the groups of the scan from partition 0 by following the links
+  const uint64_t t = blockIdx.x, T = gridDim.x;
+  const uint64_t L = lo + ((hi - lo) * (t + 1)) / T;
+  for (uint32_t j = threadIdx.x; j < K; j += kSearchThreads)
+    nxt[j] = (uint16_t)greedy_next(P, K, j, L, op.over);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t g = 0, j = 0;
+    while (j < K && g <= k) {
+      j = nxt[j];
+      ++g;
+    }
+    if (g <= k) atomicMin((unsigned long long*)&op.search[2], (unsigned long long)t);
+  }
+}
+
+__global__ void k_group_narrow(Overpart op, uint64_t T) {
+  const uint64_t lo = op.search[0], hi = op.search[1];
+  if (lo >= hi) return;
+  const uint64_t t = op.search[2];  // < T: the candidate hi is feasible
+  const uint64_t span = hi - lo;
+  op.search[1] = lo + (span * (t + 1)) / T;
+  op.search[0] = t == 0 ? lo : lo + (span * t) / T + 1;
+  op.search[2] = ~0ull;
+}
+
+__global__ void __launch_bounds__(kGreedyThreads, 1)
+k_group_finish(LevelSeg* segs, uint64_t* ssk, uint32_t* ssi, Overpart op) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const LevelSeg sg = segs[0];
+  const uint32_t k = sg.k, K = k * op.over;
+  uint32_t* P = (uint32_t*)smem_raw;                 // [K + 1]
+  uint32_t* first = P + K + 1;                       // [k + 1]
+  uint16_t* nxt = (uint16_t*)(first + k + 1);        // [K] (K <= kMaxFine < 2^16)
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t j = tid; j <= K; j += kGreedyThreads) P[j] = op.prefix[j];
+  __syncthreads();
+  // the end of the group that would start at every fine partition, in
+  // parallel; the scan from partition 0 then only follows these links
+  const uint64_t L = op.search[1];  // == search[0] once settled; always feasible
+  for (uint32_t j = tid; j < K; j += kGreedyThreads)
+    nxt[j] = (uint16_t)greedy_next(P, K, j, L, op.over);
+  __syncthreads();
   if (tid == 0) {
     uint32_t g = 0, j = 0;
     while (j < K && g < k) {
       first[g++] = j;
-      j = greedy_next(P, K, j, lo, guess);
+      j = nxt[j];
     }
     if (g == 0) first[g++] = 0;
     for (; g <= k; ++g) first[g] = K;
@@ -1577,8 +1632,15 @@ void launch_overpartition(const LaunchEnv& e, const LevelParams& P, LevelSeg* se
   }
   {
     Scope sc(e, "L1.group");
-    k_group_greedy<<<1, kGreedyThreads, greedy_smem_bytes(K, k), e.stream>>>(
-        segs, ssk, ssi, op);
+    k_group_prep<<<1, kGreedyThreads, 0, e.stream>>>(segs, op);
+    const int grid = e.num_sms * 3;
+    for (int r = 0; r < kSearchRounds; ++r) {
+      k_group_search<<<grid, kSearchThreads, (size_t)(K + 1) * 4 + (size_t)K * 2, e.stream>>>(
+          segs, op);
+      k_group_narrow<<<1, 1, 0, e.stream>>>(op, (uint64_t)grid);
+    }
+    k_group_finish<<<1, kGreedyThreads, greedy_smem_bytes(K, k), e.stream>>>(segs, ssk, ssi,
+                                                                               op);
   }
 }
 
@@ -1637,7 +1699,9 @@ void set_partition_kernel_attributes() {
   }
   cudaFuncSetAttribute(k_fine_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)fine_smem_bytes(kMaxFine));
-  cudaFuncSetAttribute(k_group_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_group_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((kMaxFine + 1) * 4 + kMaxFine * 2));
+  cudaFuncSetAttribute(k_group_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)greedy_smem_bytes(kMaxFine, kMaxK));
   cudaGetLastError();  // a refused attribute only disables the variant
   const size_t w = umax64(wd_smem_bytes(kMaxK, 0), wd_smem_bytes(kMaxK, 1));

@@ -623,7 +623,7 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   p.need_tmp = false;
   if (over > 1) {
     p.samp_extra = (uint64_t)kk + 2;
-    p.fine_cap = K;
+    p.fine_cap = 2 * (uint64_t)K + 8;  // counters, prefix sums, search state
   }
   layout(p);
   Workspace& ws = c->ws;
@@ -637,7 +637,14 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   Src src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
   src.bid = at<uint16_t>(ws, p.off_bid);
   Dst dst{(uint64_t*)d_keys_out, d_pos_out};
-  Overpart op{k, over, at<uint32_t>(ws, p.off_fine), d_fine_out, d_first_out};
+  uint32_t* fine = at<uint32_t>(ws, p.off_fine);
+  Overpart op{k,
+              over,
+              fine,
+              fine + K,
+              reinterpret_cast<uint64_t*>(fine + 2 * (uint64_t)K + 2),
+              d_fine_out,
+              d_first_out};
   launch_level(e, P, st, list1, at<SegIn>(ws, p.off_list0), at<LevelSeg>(ws, p.off_segs), src,
                dst, kWhereOut, at<uint64_t>(ws, p.off_samp_key), at<uint32_t>(ws, p.off_samp_idx),
                at<uint64_t>(ws, p.off_ssamp_key), at<uint32_t>(ws, p.off_ssamp_idx),

@@ -146,6 +146,8 @@ struct Overpart {
   uint32_t k;            // outputs (the segment's k)
   uint32_t over;         // b >= 2
   uint32_t* fine_cnt;    // [b*k] scratch counters (cleared by the launch)
+  uint32_t* prefix;      // [b*k + 1] scratch: prefix sums of the fine sizes
+  uint64_t* search;      // [3] scratch: bracket of the greedy's bound, best candidate
   uint64_t* fine_out;    // [b*k] fine partition sizes, or nullptr
   uint32_t* first_out;   // [k+1] first fine partition of every output, or nullptr
 };
