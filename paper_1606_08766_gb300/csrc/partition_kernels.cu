@@ -1341,8 +1341,8 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
 //                   splitters of the ordinary k-way step, and the segment is
 //                   pointed at them
 // ---------------------------------------------------------------------------
-constexpr int kFineThreads = 512;
-constexpr int kFineItems = 8;
+constexpr int kFineThreads = 1024;
+constexpr int kFineItems = 4;
 constexpr int kGreedyThreads = 1024;
 
 __host__ __device__ inline size_t fine_smem_bytes(uint32_t K) {
