@@ -3,7 +3,11 @@
 // arXiv 1606.08766) over a device-resident list of segments:
 //
 //   plan -> sample -> sort the sample -> classify + per-chunk histograms ->
-//   exclusive scan -> stable scatter -> collect the buckets
+//   exclusive scan -> scatter -> collect the buckets
+//
+// The scatter keeps input order inside every bucket (the partition step's
+// layout) unless the level is a full sort's deeper level, which may rank by
+// shared-memory atomics instead (the in-SM sort orders (key, position) pairs).
 //
 // Every segment of the level is partitioned independently; all segments share
 // the launches, so one level of a plain sort (one segment) and of a batched
@@ -69,6 +73,8 @@ __device__ __forceinline__ uint64_t load_key(const Src& s, uint64_t pos) {
 //          key) giving, for every bin, the range of splitters whose key falls
 //          in it; a key is located by one table read and a binary search over
 //          its bin's splitters (a full binary search when keys cluster).
+// A key equal to splitter keys is then placed among the run of those
+// splitters by its position (tie_break).
 // ---------------------------------------------------------------------------
 constexpr int kTableBitsMax = 12;
 
