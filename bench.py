@@ -169,24 +169,29 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    keys = instances.generate("uniform", N_KEYS, p=P_VIRTUAL, seed=1)
+    n = args.n
+    chunk = min(REF_SAMPLE, max(1, n // 2))
+    keys = instances.generate("uniform", n, p=P_VIRTUAL, seed=1)
     times = []
     for step in range(args.warmup + args.steps):
-        lo = (step * REF_SAMPLE) % (N_KEYS - REF_SAMPLE)
-        sample = np.ascontiguousarray(keys[lo:lo + REF_SAMPLE])
+        lo = (step * chunk) % max(1, n - chunk)
+        sample = np.ascontiguousarray(keys[lo:lo + chunk])
         t0 = time.perf_counter()
         oracle.sort(sample)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
     ms = 1e3 * statistics.mean(times)
-    value = REF_SAMPLE / (ms / 1e3) / 1e9
-    sample_desc = f"{REF_SAMPLE} consecutive keys of the 2^28 Uniform input per step"
+    value = chunk / (ms / 1e3) / 1e9
+    sample_desc = (f"{chunk} consecutive keys of the n = {n} Uniform input per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_KEYS, "p": P_VIRTUAL},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_KEYS else
+                   f"Uniform uint64 keys, n={n}, p={P_VIRTUAL} virtual partitions, seed 1",
+                   "n": n, "p": P_VIRTUAL},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
