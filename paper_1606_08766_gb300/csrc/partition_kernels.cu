@@ -968,12 +968,19 @@ k_scatter(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
           __syncwarp();
         }
         uint32_t peers = __ballot_sync(0xffffffffu, v);
+        // every lane kept its own slot: the warp's buckets are distinct, so
+        // each lane is its bucket's only peer (the common case for k >> 32)
+        const bool alone = k > 32 && __all_sync(0xffffffffu, !v || w == (uint32_t)lane);
+        if (alone) {
+          peers &= 1u << lane;
+        } else {
 #pragma unroll
-        for (int bit = 0; bit < 5; ++bit) {
-          if (bit < nbits) {
-            const bool one = (w >> bit) & 1u;
-            const uint32_t m = __ballot_sync(0xffffffffu, one);
-            peers &= one ? m : ~m;
+          for (int bit = 0; bit < 5; ++bit) {
+            if (bit < nbits) {
+              const bool one = (w >> bit) & 1u;
+              const uint32_t m = __ballot_sync(0xffffffffu, one);
+              peers &= one ? m : ~m;
+            }
           }
         }
         const uint32_t c0 = v ? my_cnt[b] : 0;
