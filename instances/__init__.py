@@ -11,7 +11,7 @@ state ``splitmix64(seed, instance_id)``.
 
 The instance names follow the Helman et al. inputs that the paper runs
 (Section 6 and Appendix "Experimental Results"); where the paper's wording is
-incomplete the readings below are used (they are listed in the design doc):
+incomplete the readings below are used:
 
 * partition ``i`` of ``p`` holds positions ``[floor(i*n/p), floor((i+1)*n/p))``
   (element ``e`` is in partition ``floor(e*p/n)``);

@@ -45,7 +45,7 @@
  *                      middle k, the root flips a coin between its two middle
  *                      entries.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - phi: 64-bit floating-point elements (Appendix "Experimental Results") are
  *     ordered by their IEEE-754 bit pattern mapped to an unsigned integer
  *     (negative: all bits flipped; non-negative: sign bit flipped), so
