@@ -66,6 +66,14 @@ typedef struct {
     uint64_t level_elems[4]; /* elements partitioned at levels 1..4 (0: unused)  */
     uint64_t class_elems[5]; /* elements handed to the in-SM sort by size class:
                                 copy-through, <= 1024, <= 2048, <= 4096, larger */
+    uint64_t algo_elems[6];  /* elements finished by each in-SM algorithm (the
+                                size-dependent choice of Section 6): [0]
+                                rank-by-counting, [1] equal-width bins, [2]
+                                bitonic (clustered keys), [3] quicksort
+                                (medium_sort = 1), [4] oversize merge sort, [5]
+                                all keys equal and already in position order.
+                                Copy-through buckets (class_elems[0]) are not
+                                sorted and are not counted here.             */
 } rsort_stats;
 
 /* Creates a context on CUDA device `device`.  hbm_budget_bytes caps the scratch
@@ -199,12 +207,12 @@ rsort_status rsort_segmented(rsort_ctx *ctx, rsort_key_type type, const void *d_
 
 /* Allocation-free variant of rsort_partition (the paper has no counterpart;
  * this is a library-level convenience).  It exists for callers that cannot
- * allocate device memory at the moment they partition: code running while a
- * CUDA graph is captured in a strict capture mode, frameworks whose device
- * memory must all come from their own allocator, and real-time loops that
- * forbid allocation after start-up.  It needs no context.
- *   - Same arguments, result and errors as rsort_partition (caller-owned
- *     inputs and outputs), on the CURRENT device and the given stream.
+ * allocate device memory at the moment they partition: frameworks whose
+ * device memory must all come from their own allocator (which would not see
+ * an allocation made here), and real-time loops that forbid allocation after
+ * start-up because an allocation can block.  It needs no context.
+ *   - Same arguments and result as rsort_partition (caller-owned inputs and
+ *     outputs), on the CURRENT device and the given stream.
  *   - Scratch comes from one fixed 8 MiB device array inside librsort that
  *     every GPU loading the library holds until the process exits.  Limit:
  *     k <= 1024 (any n <= 2^32 - 1); larger k returns RSORT_EINVAL.
@@ -213,7 +221,11 @@ rsort_status rsort_segmented(rsort_ctx *ctx, rsort_key_type type, const void *d_
  *   - Every call uses the same array (its contents persist between calls and
  *     are re-initialised by each call), so calls whose work overlaps on the
  *     GPU (other streams, other host threads) race: serialise them.
- *   - It calls no cudaMalloc, cudaFree or other allocating routine. */
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Errors: EINVAL (arguments, k > 1024), ECUDA (a launch failed).  It
+ *     reads nothing back from the device, so device-side capacity flags are
+ *     not reported; none can be raised, because the host sizes every scratch
+ *     region for the largest plan the device computes from (n, k). */
 rsort_status rsort_partition_noalloc(rsort_key_type type, const void *d_keys_in, uint64_t n,
                                      uint32_t k, uint64_t seed, void *d_keys_out,
                                      uint32_t *d_pos_out, uint64_t *d_offsets_out,

@@ -242,3 +242,151 @@ def segmented_f64(num_segments: int, max_log2: int, seed: int = 1, dup_frac: flo
         idx = np.nonzero(pick)[0]
         keys[idx] = keys[src[idx]]
     return keys.view(U64), offsets
+
+
+# ---------------------------------------------------------------------------
+# The same instances drawn with torch on any device (the GPU for full-size
+# inputs).  Integer instances give the same bytes as generate(); the Gaussian
+# one may differ in the last bits where the device's log / sqrt / cos round
+# differently from numpy's.  Keys are returned as int64 tensors holding the
+# uint64 bit patterns.  uint64 arithmetic is done on int64: additions and
+# products wrap modulo 2**64 alike, right shifts are masked to be logical,
+# and remainders are corrected for patterns above 2**63.
+# ---------------------------------------------------------------------------
+
+def _s64(v: int) -> int:
+    v &= _MASK
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def _t_shr(x, s: int):
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(x, s), (1 << (64 - s)) - 1)
+
+
+def t_splitmix64(state: int, counters):
+    """splitmix64 outputs for an int64 tensor of counters (wrapping uint64)."""
+    z = counters + 1
+    z = z * _s64(0x9E3779B97F4A7C15) + _s64(state)
+    z = torch_xor(z, _t_shr(z, 30)) * _s64(0xBF58476D1CE4E5B9)
+    z = torch_xor(z, _t_shr(z, 27)) * _s64(0x94D049BB133111EB)
+    return torch_xor(z, _t_shr(z, 31))
+
+
+def torch_xor(a, b):
+    import torch
+    return torch.bitwise_xor(a, b)
+
+
+def _t_umod(r, m: int):
+    """r (int64 holding uint64 patterns) modulo m, 0 < m < 2**64."""
+    import torch
+    if not 0 < m <= _MASK:
+        raise ValueError("modulus out of range")
+    if m >= (1 << 63):
+        # r < 2**64 < 2m: subtract m once when r >= m (unsigned compare by
+        # flipping the sign bits)
+        ms = _s64(m)
+        sign = _s64(1 << 63)
+        below = torch.bitwise_xor(r, sign) < (ms ^ sign)
+        return torch.where(below, r, r - ms)
+    a = torch.remainder(r, m)                 # r mod m for r read as signed
+    c = (1 << 64) % m                         # patterns below zero are r + 2**64
+    neg = r < 0
+    up = torch.where(a >= m - c, a - (m - c), a + c)
+    return torch.where(neg, up, a)
+
+
+def _t_partition_of(e, n: int, p: int):
+    return (e * p) // n
+
+
+def generate_torch(name: str, n: int, p: int = 1024, seed: int = 1, g: int = 32,
+                   device="cpu"):
+    """Keys of instance ``name`` as an int64 tensor on ``device`` (bit patterns
+    of the uint64 keys that generate() returns)."""
+    import torch
+    if name not in _IDS:
+        raise ValueError(f"unknown instance {name!r}; known: {NAMES}")
+    if n < 0 or n > 0xFFFFFFFF:
+        raise ValueError("n must be in [0, 2**32 - 1]")
+    dev = torch.device(device)
+    if n == 0:
+        return torch.empty(0, dtype=torch.int64, device=dev)
+    st = _stream(seed, name)
+    w = _slice_width(p)
+    e = torch.arange(n, dtype=torch.int64, device=dev)
+
+    if name == "uniform":
+        return t_splitmix64(st, e)
+
+    if name == "gaussian":
+        r1 = t_splitmix64(st, 2 * e)
+        r2 = t_splitmix64(st, 2 * e + 1)
+        u1 = (_t_shr(r1, 11).to(torch.float64) + 1.0) * 2.0 ** -53
+        u2 = _t_shr(r2, 11).to(torch.float64) * 2.0 ** -53
+        del r1, r2
+        z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+        v = torch.round(2.0 ** 63 + 2.0 ** 60 * z)
+        hi = v >= 2.0 ** 63
+        # values at or above 2**63: subtract it (exact) and set the top bit
+        lo_part = torch.where(hi, v - 2.0 ** 63, v).clamp(min=0.0)
+        lo_part = torch.where(lo_part >= 2.0 ** 63, torch.full_like(lo_part, 2.0 ** 63 - 1024),
+                              lo_part)
+        out = lo_part.to(torch.int64)
+        out = torch.where(hi, torch.bitwise_xor(out, _s64(1 << 63)), out)
+        out = torch.where(v >= 2.0 ** 64, torch.full_like(out, -1), out)
+        out = torch.where(v <= 0.0, torch.zeros_like(out), out)
+        return out
+
+    if name == "reverse":
+        ws = _MASK // n
+        return (n - 1 - e) * _s64(ws) + _t_umod(t_splitmix64(st, e), ws)
+
+    if name in ("bucket_sorted", "staggered", "all_to_one", "g_group"):
+        part = _t_partition_of(e, n, p)
+        if name == "bucket_sorted":
+            sl = part
+        elif name == "staggered":
+            half = p // 2
+            sl = torch.where(part < half, 2 * part + 1, 2 * (part - half))
+        elif name == "all_to_one":
+            sl = torch.zeros_like(part)
+        else:
+            local = e - (part * n + (p - 1)) // p
+            sl = torch.remainder((part // g) * g + p // 2 + torch.remainder(local, g), p)
+        return sl * _s64(w) + _t_umod(t_splitmix64(st, e), w)
+
+    if name == "mirrored":
+        first = n - n // 2
+        out = torch.empty(n, dtype=torch.int64, device=dev)
+        out[:first] = t_splitmix64(st, e[:first])
+        if n // 2:
+            out[first:] = torch.flip(out[: n // 2], dims=(0,))
+        return out
+
+    if name == "zero":
+        return torch.zeros(n, dtype=torch.int64, device=dev)
+
+    if name == "rand_dupl":
+        lengths, values = [], []
+        total = 0
+        r = 0
+        while total < n:
+            batch = max(16, (n - total) // 2048 + 16)
+            c = torch.arange(r, r + batch, dtype=torch.int64, device=dev)
+            rl = t_splitmix64(st, 2 * c)
+            rv = t_splitmix64(st, 2 * c + 1)
+            lengths.append(torch.bitwise_and(rl, 4095) + 1)
+            values.append(torch.bitwise_and(rv, 15))
+            total += int(lengths[-1].sum().item())
+            r += batch
+        return torch.repeat_interleave(torch.cat(values), torch.cat(lengths))[:n].contiguous()
+
+    if name == "deter_dupl":
+        # floor(log2(partition + 1)), one value per partition
+        table = torch.tensor([(i + 1).bit_length() - 1 for i in range(p)], dtype=torch.int64,
+                             device=dev)
+        return table[_t_partition_of(e, n, p)]
+
+    raise AssertionError(name)

@@ -17,6 +17,9 @@ from . import build as _build
 KEY_U64 = 0
 KEY_F64 = 1
 
+# rsort_stats.algo_elems: elements finished by each in-SM algorithm
+ALGO_NAMES = ("rank", "bins", "bitonic", "quicksort", "merge", "in_order")
+
 _STATUS = {0: "ok", 1: "pending", -1: "invalid argument", -2: "out of memory",
            -3: "CUDA error", -4: "timed out", -5: "cancelled", -6: "unsupported",
            -7: "device-side error"}
@@ -35,7 +38,7 @@ class _Stats(ctypes.Structure):
                 ("path", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
                 ("max_over_mean", ctypes.c_double), ("final_buckets", ctypes.c_uint64),
                 ("bytes_moved", ctypes.c_uint64), ("level_elems", ctypes.c_uint64 * 4),
-                ("class_elems", ctypes.c_uint64 * 5)]
+                ("class_elems", ctypes.c_uint64 * 5), ("algo_elems", ctypes.c_uint64 * 6)]
 
 
 class _PartOpts(ctypes.Structure):
@@ -70,6 +73,7 @@ class Stats:
     bytes_moved: int
     level_elems: list
     class_elems: list
+    algo_elems: list
 
 
 def library_path() -> str:
@@ -161,6 +165,19 @@ def partition_noalloc(keys: torch.Tensor, k: int, seed: int, keys_out: torch.Ten
     lib = load_library()
     _check_keys(keys)
     n = keys.numel()
+    dev = torch.cuda.current_device()
+    for name, t in (("keys", keys), ("keys_out", keys_out), ("pos_out", pos_out),
+                    ("offsets_out", offsets_out)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{dev})")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    if keys_out.dtype != keys.dtype:
+        raise ValueError("keys_out must have the dtype of keys")
+    if pos_out.dtype != torch.int32:
+        raise ValueError("pos_out must be int32 (it holds uint32 positions)")
+    if offsets_out.dtype != torch.int64:
+        raise ValueError("offsets_out must be int64")
     if keys_out.numel() != n or pos_out.numel() != n or offsets_out.numel() != k + 1:
         raise ValueError("output sizes do not match n and k")
     rc = lib.rsort_partition_noalloc(_key_type(keys, key_type), _ptr(keys), n, k,
@@ -216,7 +233,8 @@ class Context:
         if stats:
             return keys_out, perm_out, Stats(st.n, st.p, st.levels, st.path, st.max_bucket,
                                              st.max_over_mean, st.final_buckets, st.bytes_moved,
-                                             list(st.level_elems), list(st.class_elems))
+                                             list(st.level_elems), list(st.class_elems),
+                                             list(st.algo_elems))
         return keys_out, perm_out
 
     def sort_raw(self, key_type: int, d_in: int, d_out: int, d_perm: int, n: int, p: int,

@@ -108,7 +108,8 @@ __device__ void cta_quicksort_pairs(const QsSmem& q, uint32_t m, uint64_t seed,
           idx[r] = q.ai[lo + e];
         }
       }
-      cta_sort_pairs<NT, kBaseItems>(key, idx, len, [] { return false; }, q.base, red, scan_sm);
+      cta_sort_pairs<NT, kBaseItems>(key, idx, len, [] { return false; }, q.base, red, scan_sm,
+                                     nullptr);
       for (uint32_t t = tid; t < len; t += NT) {
         q.ak[lo + t] = q.base.k[t];
         q.ai[lo + t] = q.base.i[t];

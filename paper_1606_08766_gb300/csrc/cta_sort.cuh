@@ -84,17 +84,26 @@ __device__ __forceinline__ void restore_common_key(const CtaSortSmem& s, uint32_
   __syncthreads();
 }
 
+// Adds the m elements of a bucket to the counter of the algorithm that sorted
+// it (algo: kNumAlgos counters, or nullptr when nobody counts).
+__device__ __forceinline__ void count_algo(uint64_t* algo, int which, uint32_t m) {
+  if (algo && threadIdx.x == 0) atomicAdd((unsigned long long*)&algo[which], (unsigned long long)m);
+}
+
 // Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
 // in_position_order() says whether the elements arrive with increasing
-// positions; it is asked only when all keys are equal.
+// positions; it is asked only when all keys are equal.  algo (nullable) gets
+// m added to the counter of the branch taken (kAlgoRank, kAlgoInOrder,
+// kAlgoBitonic or kAlgoBins).
 template <int NT, int ITEMS, typename InOrderFn>
 __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], uint32_t m,
                                InOrderFn in_position_order, const CtaSortSmem& s, uint64_t* red,
-                               uint64_t* scan_sm) {
+                               uint64_t* scan_sm, uint64_t* algo) {
   constexpr uint32_t kCap = NT * ITEMS;
   static_assert(ITEMS >= 4, "the padded counters need cap/4 >= NT words of slack");
   const uint32_t tid = threadIdx.x;
   if (m <= (uint32_t)kRankMax) {
+    count_algo(algo, kAlgoRank, m);
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const uint32_t e = r * NT + tid;
@@ -120,6 +129,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   }
   block_minmax_u64<NT>(mn, mx, red);
   if (mn == mx && in_position_order()) {
+    count_algo(algo, kAlgoInOrder, m);
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
       const uint32_t e = r * NT + tid;
@@ -199,6 +209,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   }
   if (__syncthreads_or(crowd)) {
     // clustered keys: bitonic sort of the whole bucket
+    count_algo(algo, kAlgoBitonic, m);
     const uint32_t P = next_pow2_u32(m);
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
@@ -212,6 +223,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   }
   // counting-sort scatter into the bins; the second element to land in a bin
   // puts the bin on the list of bins that still need ordering
+  count_algo(algo, kAlgoBins, m);
   uint32_t* multi = s.hist + kCap + kCap / 4;
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {

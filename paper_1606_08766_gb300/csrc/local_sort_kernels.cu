@@ -189,7 +189,7 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   }
   while (it >= 0) {
     cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
-                           red, scan_sm);
+                           red, scan_sm, st->algo_elems);
     // claim and start loading the next bucket before this one is stored, so
     // its loads are in flight while the stores go out
     const int64_t it2 = next_item(st, CLS, cap, &s_item);
@@ -222,6 +222,7 @@ k_local_quicksort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B, ui
     const int64_t it = next_item(st, CLS, cap, &s_item);
     if (it < 0) break;
     const FinalItem f = list[it];
+    count_algo(st->algo_elems, kAlgoQuick, f.size);
     for (uint32_t t = threadIdx.x; t < f.size; t += NT) {
       uint64_t k;
       uint32_t i;
@@ -267,6 +268,7 @@ k_local_big(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   for (;;) {
     const int64_t it = next_item(st, kClassBig, cap, &s_item);
     if (it < 0) break;
+    count_algo(st->algo_elems, kAlgoMerge, list[it].size);
     sort_big(B, list[it], sk, si);
   }
 }

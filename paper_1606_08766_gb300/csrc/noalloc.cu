@@ -3,11 +3,16 @@
 // library allocates.
 //
 // Why it exists: some callers cannot allocate device memory at the time they
-// need to partition -- code that runs while a CUDA graph is being captured in
-// the strict capture modes, callers whose device memory is owned by another
+// need to partition -- callers whose device memory is owned by another
 // allocator that must see every allocation, and real-time loops that forbid
-// any allocation after start-up.  They still pass their own inputs and outputs;
-// only the scratch (samples, histograms, the control block) comes from here.
+// any allocation after start-up because an allocation can block.  They still
+// pass their own inputs and outputs; only the scratch (samples, histograms,
+// the control block) comes from here.
+//
+// The host plan below sizes every region for the largest plan k_level_plan
+// computes from (n, k): the same sample count, chunk count, histogram and
+// bucket count, so the device-side capacity checks never fire.  Nothing is
+// read back from the device, so a device flag would go unreported.
 //
 // The scratch is one file-scope __device__ array of kNoAllocBytes (8 MiB).
 // Every GPU that loads librsort holds it until the process exits.  In host

@@ -307,6 +307,7 @@ __global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uin
     st->cursor_c[c] = 0;
     st->class_elems[c] = 0;
   }
+  for (int a = 0; a < kNumAlgos; ++a) st->algo_elems[a] = 0;
   st->error = 0;
   st->max_bucket_l1 = 0;
   st->levels_used = 0;
@@ -498,7 +499,8 @@ k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_ke
         idx[r] = samp_idx[base + e];
       }
     }
-    cta_sort_pairs<NT, IT>(key, idx, len, [&] { return in_order != 0; }, s, red, scan_sm);
+    cta_sort_pairs<NT, IT>(key, idx, len, [&] { return in_order != 0; }, s, red, scan_sm,
+                           nullptr);
     uint64_t* ok = sg.nschunks == 1 ? ssamp_key : samp_key;
     uint32_t* oi = sg.nschunks == 1 ? ssamp_idx : samp_idx;
     for (uint32_t t = threadIdx.x; t < len; t += NT) {

@@ -752,6 +752,8 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
     opt_stats->bytes_moved = bytes;
     static_assert(kNumClasses == 5, "rsort_stats.class_elems has one entry per size class");
     for (int i = 0; i < kNumClasses; ++i) opt_stats->class_elems[i] = h.class_elems[i];
+    static_assert(kNumAlgos == 6, "rsort_stats.algo_elems has one entry per in-SM algorithm");
+    for (int i = 0; i < kNumAlgos; ++i) opt_stats->algo_elems[i] = h.algo_elems[i];
     if (h.error) return latch(c, RSORT_EDEVICE);
   }
   return RSORT_OK;

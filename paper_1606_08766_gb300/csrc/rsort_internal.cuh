@@ -50,6 +50,17 @@ enum : int {
   kClassBig = 4,
   kNumClasses = 5
 };
+// Which in-SM algorithm finished a bucket (rsort_stats.algo_elems counts the
+// elements each one handled):
+enum : int {
+  kAlgoRank = 0,     // rank-by-counting (tiny buckets)
+  kAlgoBins = 1,     // equal-width bins + ranking inside crowded-free bins
+  kAlgoBitonic = 2,  // bitonic sort (a bin held more than kBinLimit keys)
+  kAlgoQuick = 3,    // quicksort with tree-median pivots (opt-in medium path)
+  kAlgoMerge = 4,    // oversize merge sort through global memory
+  kAlgoInOrder = 5,  // all keys equal and already in position order
+  kNumAlgos = 6
+};
 constexpr uint32_t kSmallCap = 1024;
 constexpr uint32_t kMidCap = 2048;
 
@@ -95,6 +106,7 @@ struct DevState {
   uint32_t nfinal_c[kNumClasses];  // final items per size class
   uint32_t cursor_c[kNumClasses];  // work counters of the in-SM sort kernels
   uint64_t class_elems[kNumClasses];  // elements handed to each size class
+  uint64_t algo_elems[kNumAlgos];     // elements finished by each in-SM algorithm
   uint32_t error;           // capacity / wait errors (bit flags)
   uint32_t max_bucket_l1;   // largest level-1 bucket
   uint32_t levels_used;

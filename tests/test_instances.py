@@ -81,3 +81,20 @@ def test_all_names_small_sizes(name):
     for n in (0, 1, 2, 3, 100):
         a = instances.generate(name, n, p=8)
         assert a.shape == (n,) and a.dtype == np.uint64
+
+
+@pytest.mark.parametrize("name", instances.NAMES)
+@pytest.mark.parametrize("n,p", [(1, 1024), (3, 2), (1000, 7), (65537, 1024), (40000, 1)])
+def test_torch_generator_matches_numpy(name, n, p):
+    """The torch generator (used on the GPU for full-size inputs) draws the
+    same keys as the numpy one; the Gaussian instance may differ in the last
+    bits of the rounding (at most a few units of 2^11, the spacing of float64
+    values near 2^63)."""
+    import torch  # noqa: F401
+    a = instances.generate(name, n, p=p, seed=3)
+    b = instances.generate_torch(name, n, p=p, seed=3).numpy().view(np.uint64)
+    if name == "gaussian":
+        assert np.abs(a.astype(np.float64) - b.astype(np.float64)).max() <= 4096
+        assert np.count_nonzero(a != b) <= max(1, n // 1000)
+    else:
+        np.testing.assert_array_equal(a, b)
