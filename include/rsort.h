@@ -330,6 +330,13 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                rank-by-counting; 1 in-SM quicksort whose pivots are the
  *                binary-tree median approximation (see rsort_approx_median)
  *                of a 256-element stratified sample of each segment.
+ *   unit_scatter  1 (default): a level that keeps input order inside buckets
+ *                (level 1, the partition step) and has at most 1024 buckets
+ *                stores every element's bucket id when it classifies, and
+ *                its scatter writes whole 8-element units (64 bytes of keys,
+ *                32 bytes of positions), holding each bucket's incomplete
+ *                last unit in shared memory; 0: the staged scatter, which
+ *                classifies again.
  *   wide_scatter_k  levels with at least this many buckets stage 4096-key
  *                sub-tiles with 512 threads when shared memory allows
  *                (default 1024).

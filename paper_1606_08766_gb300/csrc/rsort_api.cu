@@ -106,6 +106,7 @@ struct Plan {
   int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
   int wide_scatter_k = 1024;  // levels with at least this many buckets use wide sub-tiles
   uint32_t target_bucket = kTargetBucket;  // automatic fan-out target
+  int unit_scatter = 1;     // stored bucket ids + whole-unit scatter where it fits
   uint64_t samp_extra = 0;  // sorted-sample slots past the sample (overpartitioning)
   uint64_t fine_cap = 0;    // fine partition counters (overpartitioning)
   // arena offsets
@@ -212,6 +213,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level
   P.warp_direct = kmax_level <= p.wd_max_k ? 1 : 0;
   P.wide_scatter_k = p.wide_scatter_k;
   P.target_bucket = p.target_bucket;
+  P.unit_scatter = p.unit_scatter;
   return P;
 }
 
@@ -242,6 +244,7 @@ void set_attributes_once(int device) {
     if (d == device) return;
   set_partition_kernel_attributes();
   set_local_kernel_attributes();
+  set_unit_scatter_attributes();
   done.push_back(device);
 }
 
@@ -312,6 +315,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   if (strcmp(name, "medium_sort") == 0) {
     if (v != 0 && v != 1) return RSORT_EINVAL;
     c->medium_sort = (int)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "unit_scatter") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->unit_scatter = (int)v;
     return RSORT_OK;
   }
   if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
@@ -389,6 +397,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  p.unit_scatter = c->unit_scatter;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (n <= (uint64_t)kBucketCap) {
     p.n = n;
@@ -411,6 +420,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  p.unit_scatter = c->unit_scatter;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, c->max_levels);
   p.final_cap += num_segments;
@@ -617,6 +627,7 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  p.unit_scatter = c->unit_scatter;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -857,6 +868,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "medium_sort") == 0) {
     *value = c->medium_sort;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "unit_scatter") == 0) {
+    *value = c->unit_scatter;
     return RSORT_OK;
   }
   if (strcmp(name, "serve_batch_keys") == 0) {

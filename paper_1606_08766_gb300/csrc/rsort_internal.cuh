@@ -31,6 +31,7 @@ constexpr int kLocalThreads = 256;                // in-SM bucket sort CTA
 constexpr int kLocalItems = 16;                   // kLocalThreads * kLocalItems = kBucketCap
 constexpr int kRankMax = 64;                      // rank-by-counting up to this size
 constexpr int kScanTile = 4096;                   // device scan tile (1024 x 4)
+constexpr int kUnitMaxK = 1024;                   // buckets of the whole-unit scatter
 
 // Where the elements of a final bucket live.
 enum : uint16_t { kWhereOut = 0, kWhereTmp = 1, kWhereInput = 2 };
@@ -149,6 +150,9 @@ struct LevelParams {
                           // (key, position) pairs, so the result is the same)
   int in_order = 1;       // 1: the level's segments hold their elements in
                           // position order (level 1, or after a stable level)
+  int unit_scatter = 1;   // 1: a stable level with at most kUnitMaxK buckets
+                          // stores bucket ids when classifying and scatters
+                          // whole 8-element units (unit_scatter.cu)
 };
 
 // AMS-sort overpartitioning of a one-segment partition step: b*k fine
@@ -293,6 +297,10 @@ __device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint6
 }
 __host__ __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
+// Per-warp counter rows of the scatters are padded to an even length so a warp
+// can clear its row with 32-bit stores without touching the next warp's row.
+__host__ __device__ inline uint32_t cnt_stride(uint32_t kmax) { return (kmax + 1) & ~1u; }
+
 __host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
   uint32_t p = 1;
   while (p < x) p <<= 1;
@@ -342,6 +350,15 @@ bool launch_tree_median(const LaunchEnv& e, const uint64_t* keys, uint32_t n, in
 void launch_plain_groups(const LaunchEnv& e, const uint64_t* offsets, uint32_t k,
                          uint64_t* fine_out, uint32_t* first_out);
 void set_local_kernel_attributes();
+// Classify with stored bucket ids and the whole-unit scatter (unit_scatter.cu).
+void set_unit_scatter_attributes();
+bool unit_scatter_fits(uint32_t kmax);
+void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                         const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t* ssi,
+                         uint32_t* hist, uint32_t kmax, int mode, const char* name);
+void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                          const LevelSeg* segs, Src src, const uint32_t* hist_scan, Dst dst,
+                          uint32_t kmax, int unmap_out, const char* name);
 void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
                        uint64_t item_cap, const uint64_t* in_key, Dst out, Dst tmp, int f64);
 

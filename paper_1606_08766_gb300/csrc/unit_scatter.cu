@@ -1,0 +1,615 @@
+// unit_scatter.cu -- the classify and scatter passes of a stable partition
+// level (the data exchange of Appendix "Robust Multi-Level Sample Sort",
+// MPI_Alltoallv in the paper, a stable scatter through HBM here) with the
+// bucket of every element computed once and its output written in whole
+// sectors.
+//
+// k_classify_ids   classifies every element of a chunk once (splitters in
+//                  shared memory, the same classifiers as every other level)
+//                  and stores its bucket id (16 bits) beside the per-chunk
+//                  bucket histogram.  Keys stream through 16-byte loads (two
+//                  keys each) straight into registers.
+//
+// k_scatter_units  reads keys and stored bucket ids of 4096-element sub-tiles
+//                  (registers, the next sub-tile's loads in flight while the
+//                  current one is processed), ranks every element among the
+//                  elements of its bucket (warp order, then lane order: input
+//                  order, so buckets keep input order), counting-sorts the
+//                  sub-tile into shared memory, and writes every bucket's run
+//                  in whole UNITS of 8 elements -- 64 bytes of keys and 32
+//                  bytes of positions, aligned in the output -- each stored by
+//                  8 consecutive lanes of one warp instruction, so every output
+//                  sector is written whole and once.  A bucket's incomplete
+//                  last unit (at most 7 elements) waits in a per-bucket carry
+//                  area in shared memory and goes out with the bucket's next
+//                  elements.  Only the first and last unit of a bucket in a
+//                  chunk, shared with the neighbouring chunks' ranges, are
+//                  written in part.
+//
+// The carry area holds 7 (key, position) slots per bucket, so the scatter
+// serves levels with at most kUnitMaxK buckets.
+#include "async_copy.cuh"
+#include "rsort_internal.cuh"
+#include "splitters.cuh"
+
+namespace rsort {
+
+namespace {
+
+struct Scope {
+  const LaunchEnv& e;
+  Scope(const LaunchEnv& env, const char* name) : e(env) {
+    if (e.timer) e.timer->begin(name, e.stream);
+  }
+  ~Scope() {
+    if (e.timer) e.timer->end(e.stream);
+    if (e.launches) ++*e.launches;
+  }
+};
+
+constexpr int kUnit = 8;    // elements per output unit
+constexpr int kCarry = 7;   // carry slots per bucket (kUnit - 1)
+
+// Streaming loads of data read once: no L1 allocation, L2 evict-first.
+__device__ __forceinline__ void ld_stream_v2(uint64_t& a, uint64_t& b, const uint64_t* p,
+                                             uint64_t pol) {
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+      : "=l"(a), "=l"(b)
+      : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ uint64_t ld_stream_u64(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u16(const uint16_t* p, uint64_t pol) {
+  unsigned short v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Key bits as the level stores them: conv 1 maps float64 patterns to the
+// order map, 2 maps them back, 0 leaves them.
+__device__ __forceinline__ uint64_t conv_key(uint64_t k, int conv) {
+  return conv == 1 ? f64_to_ordered(k) : (conv == 2 ? ordered_to_f64(k) : k);
+}
+
+// ---------------------------------------------------------------------------
+// Classify with stored bucket ids
+// ---------------------------------------------------------------------------
+constexpr int kCiPairs = 4;  // 16-byte loads (two keys) per thread per step
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 3)
+k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+               const uint32_t* ssi, uint32_t* hist, uint32_t kmax, int mode, int vec) {
+  constexpr int R = 2 * kCiPairs;  // keys per thread per step
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Splitters sp;
+  uint32_t* cnt;
+  {
+    unsigned char* p = smem_raw;
+    const size_t Kp = next_pow2_u32(kmax);
+    sp.mode = mode & 1;
+    sp.ntb = (mode >> 1) & 1;
+    sp.tree = nullptr;
+    sp.tbl = nullptr;
+    if (sp.mode == 0) {
+      sp.tree = (uint64_t*)p;
+      p += Kp * 8;
+    } else {
+      sp.tbl = (uint32_t*)p;
+      p += (size_t)4 << table_bits_for((uint32_t)Kp);
+    }
+    sp.key = (uint64_t*)p; p += (size_t)kmax * 8;
+    sp.idx = (uint32_t*)p; p += (size_t)kmax * 4;
+    cnt = (uint32_t*)p; p += (size_t)kmax * 4;
+    sp.rend = (uint16_t*)p;
+  }
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31;
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    __syncthreads();
+    if (g != cur_g) {
+      load_splitters<NT>(sg, ssk, ssi, sp);
+      cur_g = g;
+    }
+    for (uint32_t b = threadIdx.x; b < sg.k; b += NT) cnt[b] = 0;
+    __syncthreads();
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
+    // pairs start at the even position at or below cs (16-byte aligned when
+    // the key array is); a pair reaches past ce only by its second element
+    const uint64_t ps = cs & ~1ull;
+    const uint64_t npairs = (ce - ps + 1) >> 1;
+    auto load = [&](uint64_t p0, uint64_t (&x)[R]) {
+#pragma unroll
+      for (int r = 0; r < kCiPairs; ++r) {
+        const uint64_t j = p0 + (uint64_t)r * NT + threadIdx.x;
+        const uint64_t pos = ps + 2 * j;
+        x[2 * r] = x[2 * r + 1] = 0;
+        if (j < npairs) {
+          if (vec && pos + 1 < ce) {
+            ld_stream_v2(x[2 * r], x[2 * r + 1], src.key + pos, pol);
+          } else {
+            x[2 * r] = ld_stream_u64(src.key + pos, pol);
+            if (pos + 1 < ce) x[2 * r + 1] = ld_stream_u64(src.key + pos + 1, pol);
+          }
+        }
+      }
+    };
+    uint64_t x[R], xn[R];
+    load(0, x);
+    for (uint64_t p0 = 0; p0 < npairs; p0 += (uint64_t)NT * kCiPairs) {
+      load(p0 + (uint64_t)NT * kCiPairs, xn);
+      uint64_t key[R];
+#pragma unroll
+      for (int e = 0; e < R; ++e) key[e] = src.map_f64 ? f64_to_ordered(x[e]) : x[e];
+      uint32_t bk[R];
+      // positions are read only on a key tie, and only inside the chunk (a
+      // padding slot's result is discarded)
+      classify_batch<R>(key, bk, [&](int e) {
+        const uint64_t pos = ps + 2 * (p0 + (uint64_t)(e >> 1) * NT + threadIdx.x) + (e & 1);
+        if (pos < cs || pos >= ce) return 0u;
+        return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
+      }, sp);
+#pragma unroll
+      for (int r = 0; r < kCiPairs; ++r) {
+        const uint64_t j = p0 + (uint64_t)r * NT + threadIdx.x;
+        const uint64_t pos = ps + 2 * j;
+        const bool v0 = j < npairs && pos >= cs;
+        const bool v1 = j < npairs && pos + 1 < ce;
+        if (v0 && v1) {
+          *reinterpret_cast<uint32_t*>(src.bid + pos) = bk[2 * r] | (bk[2 * r + 1] << 16);
+        } else if (v0) {
+          src.bid[pos] = (uint16_t)bk[2 * r];
+        } else if (v1) {
+          src.bid[pos + 1] = (uint16_t)bk[2 * r + 1];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const bool v = h ? v1 : v0;
+          const uint32_t b = bk[2 * r + h];
+          const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
+          if (__all_sync(0xffffffffu, v && b == bl)) {
+            if (lane == 0) atomicAdd(&cnt[bl], 32u);
+          } else if (v) {
+            atomicAdd(&cnt[b], 1u);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < R; ++e) x[e] = xn[e];
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < sg.k; b += NT)
+      hist[sg.hist_off + (uint64_t)b * sg.nunits + cl] = cnt[b];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Scatter in whole units
+// ---------------------------------------------------------------------------
+constexpr int kUsThreads = 512;
+constexpr int kUsItems = 8;
+constexpr int kUsTile = kUsThreads * kUsItems;  // 4096 elements per sub-tile
+
+__host__ __device__ inline uint32_t us_max_units(uint32_t kmax) {
+  return (kUsTile + kCarry * kmax) / kUnit + 1;
+}
+
+__host__ __device__ inline size_t us_smem_bytes(uint32_t kmax) {
+  constexpr int NW = kUsThreads / 32;
+  size_t b = 0;
+  b += (size_t)kUsTile * 8;                      // sorted keys
+  b += (size_t)kmax * kCarry * 8;                // carried keys
+  b += (size_t)kUsTile * 4;                      // sorted positions
+  b += (size_t)kmax * kCarry * 4;                // carried positions
+  b += (size_t)kmax * 8;                         // per-bucket obase + meta
+  b += (size_t)(kmax + 1) * 4;                   // sbase
+  b += (size_t)NW * cnt_stride(kmax) * 2;        // per-warp counters
+  b += (size_t)us_max_units(kmax) * 2 + 2;       // unit -> bucket
+  b += (size_t)NW * kmax;                        // per-warp winner slots
+  return (b + 15) & ~(size_t)15;
+}
+
+// Exclusive max-scan of one u32 per thread over the block (NT % 32 == 0);
+// sm holds NT/32 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_max_u32(uint32_t v, uint32_t* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = max(x, y);
+  }
+  if (lane == 31) sm[w] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int q = 0; q < w; ++q) pre = max(pre, sm[q]);
+  const uint32_t y = __shfl_up_sync(0xffffffffu, x, 1);
+  const uint32_t excl = max(pre, lane > 0 ? y : 0u);
+  __syncthreads();
+  return excl;
+}
+
+// HAS_IDX: the level reads stored positions (deeper levels); otherwise the
+// position is implicit (level 1: offset in the segment).
+template <int NT, bool HAS_IDX>
+__global__ void __launch_bounds__(NT, 1)
+k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_t* hist_scan,
+                Dst dst, uint32_t kmax, int conv, uint32_t aoff) {
+  constexpr int NW = NT / 32;
+  constexpr int IT = kUsItems;
+  constexpr int ST = NT * IT;
+  static_assert(ST == kUsTile, "sub-tile size");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* p = smem_raw;
+  uint64_t* skey = (uint64_t*)p; p += (size_t)ST * 8;
+  uint64_t* ckey = (uint64_t*)p; p += (size_t)kmax * kCarry * 8;
+  uint32_t* sidx = (uint32_t*)p; p += (size_t)ST * 4;
+  uint32_t* cidx = (uint32_t*)p; p += (size_t)kmax * kCarry * 4;
+  // per-bucket state (two flat word arrays, so that both the bucket-ordered
+  // and the interleaved phases touch consecutive words):
+  //   obase  output position of the bucket's current unit start (mod 2^32)
+  //   meta   sorted slot of that unit's first slot + 8 (13 bits; the unit
+  //          may begin with up to 7 carried slots) | first unit in the unit
+  //          list << 13 (11 bits) | carry count << 24 | phantoms << 27
+  uint32_t* obase = (uint32_t*)p; p += (size_t)kmax * 4;
+  uint32_t* meta = (uint32_t*)p; p += (size_t)kmax * 4;
+  uint32_t* sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4;
+  const uint32_t kst = cnt_stride(kmax);
+  uint16_t* wcnt = (uint16_t*)p; p += (size_t)NW * kst * 2;
+  const uint32_t umax = us_max_units(kmax);
+  uint16_t* unit_b = (uint16_t*)p; p += (size_t)umax * 2 + 2;
+  uint8_t* wwin = (uint8_t*)p;
+  __shared__ uint64_t scan_sm[NW];
+  __shared__ uint32_t max_sm[NW];
+
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t ltmask = lanemask_lt();
+  uint16_t* my_cnt = wcnt + (size_t)warp * kst;
+  uint8_t* my_win = wwin + (size_t)warp * kmax;
+  for (uint32_t u = tid; u < umax; u += NT) unit_b[u] = 0;
+
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    const uint32_t k = sg.k;
+    const int nbits = k > 32 ? 5 : (int)ceil_log2_dev(k);
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
+    const uint64_t nst = (ce - cs + ST - 1) / ST;
+    // buckets handled by this thread in the per-bucket phases
+    const uint32_t per = (k + NT - 1) / NT;
+    const uint32_t bb0 = min(tid * per, k);
+    const uint32_t bb1 = min(bb0 + per, k);
+    __syncthreads();  // the previous chunk is done with every shared array
+    // output state of every bucket: the chunk's first position p0, the unit
+    // start at or below it (units start at positions = aoff mod 8) and the
+    // slots before p0 in that unit (phantoms: held, never written)
+    for (uint32_t b = tid; b < k; b += NT) {
+      const uint32_t p0 = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] +
+                                     sg.delta);
+      const uint32_t a = (p0 - aoff) & (kUnit - 1);
+      obase[b] = p0 - a;
+      meta[b] = (a << 24) | (a << 27);
+    }
+    const uint32_t q0 = (uint32_t)warp * (IT * 32) + lane;
+    uint64_t key[IT], nkey[IT];
+    uint32_t idx[IT], nidx[IT], bid[IT], nbid[IT];
+    auto load = [&](uint64_t s, uint64_t (&kk)[IT], uint32_t (&ii)[IT], uint32_t (&bb)[IT]) {
+      const uint64_t b0 = cs + s * ST;
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        const uint64_t pos = b0 + q0 + r * 32;
+        kk[r] = 0;
+        ii[r] = 0;
+        bb[r] = 0xffffffffu;
+        if (s < nst && pos < ce) {
+          kk[r] = ld_stream_u64(src.key + pos, pol);
+          if (HAS_IDX) ii[r] = ld_stream_u32(src.idx + pos, pol);
+          bb[r] = ld_stream_u16(src.bid + pos, pol);
+        }
+      }
+    };
+    load(0, key, idx, bid);
+    for (uint64_t s = 0; s < nst; ++s) {
+      load(s + 1, nkey, nidx, nbid);
+      // -- 1. rank every element among its bucket's elements of this warp
+      //    (stable: earlier rounds, then lower lanes)
+      for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
+      __syncwarp();
+      uint32_t lrank[IT];
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        const uint32_t b = bid[r];
+        const bool v = b != 0xffffffffu;
+        // peers = the lanes holding the same bucket: up to 32 buckets by
+        // ballots over the bucket bits; beyond, every lane writes its lane id
+        // to the warp's slot of its bucket and the id that stayed there (one
+        // per distinct bucket) is compared instead
+        uint32_t w = b;
+        if (k > 32) {
+          if (v) my_win[b] = (uint8_t)lane;
+          __syncwarp();
+          w = v ? my_win[b] : 0u;
+          __syncwarp();
+        }
+        uint32_t peers = __ballot_sync(0xffffffffu, v);
+        const bool alone = k > 32 && __all_sync(0xffffffffu, !v || w == (uint32_t)lane);
+        if (alone) {
+          peers &= 1u << lane;
+        } else {
+#pragma unroll
+          for (int bit = 0; bit < 5; ++bit) {
+            if (bit < nbits) {
+              const bool one = (w >> bit) & 1u;
+              const uint32_t m = __ballot_sync(0xffffffffu, one);
+              peers &= one ? m : ~m;
+            }
+          }
+        }
+        const uint32_t c0 = v ? my_cnt[b] : 0;
+        __syncwarp();
+        if (v && lane == __ffs(peers) - 1) my_cnt[b] = (uint16_t)(c0 + __popc(peers));
+        __syncwarp();
+        lrank[r] = c0 + __popc(peers & ltmask);
+      }
+      __syncthreads();  // (A) every warp's counts are in
+      // -- 2. per bucket: exclusive prefix over the warps' counts (in place),
+      //    the bucket's elements t in this sub-tile, its virtual run
+      //    (carry + t) and the whole units u of that run; then one block scan
+      //    of (u, t) places every bucket's elements in the sorted sub-tile and
+      //    its units in the unit list
+      uint32_t loc_t = 0, loc_u = 0;
+      {
+        uint32_t b = bb0;
+        for (; (per & 1) == 0 && b + 1 < bb1; b += 2) {
+          uint32_t tot2 = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            uint32_t* cw = reinterpret_cast<uint32_t*>(wcnt + (size_t)w * kst + b);
+            const uint32_t cnt2 = *cw;
+            *cw = tot2;
+            tot2 = __vadd2(tot2, cnt2);
+          }
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t t = h ? (tot2 >> 16) : (tot2 & 0xffffu);
+            const uint32_t u = (((meta[b + h] >> 24) & 7u) + t) / kUnit;
+            sbase[b + h] = t | (u << 16);
+            loc_t += t;
+            loc_u += u;
+          }
+        }
+        for (; b < bb1; ++b) {
+          uint32_t t = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            const uint32_t cnt = wcnt[(size_t)w * kst + b];
+            wcnt[(size_t)w * kst + b] = (uint16_t)t;
+            t += cnt;
+          }
+          const uint32_t u = (((meta[b] >> 24) & 7u) + t) / kUnit;
+          sbase[b] = t | (u << 16);
+          loc_t += t;
+          loc_u += u;
+        }
+      }
+      uint64_t tot;
+      const uint64_t ex =
+          block_excl_scan_u64<NT>(((uint64_t)loc_u << 32) | loc_t, &tot, scan_sm);
+      {
+        uint32_t run_t = (uint32_t)ex, run_u = (uint32_t)(ex >> 32);
+        for (uint32_t b = bb0; b < bb1; ++b) {
+          const uint32_t tu = sbase[b], t = tu & 0xffffu, u = tu >> 16;
+          const uint32_t m = meta[b];
+          const uint32_t cb = (m >> 24) & 7u;
+          sbase[b] = run_t;
+          meta[b] = (m & 0xff000000u) | (run_u << 13) | (run_t + kUnit - cb);
+          if (u) unit_b[run_u] = (uint16_t)(b + 1);
+          run_t += t;
+          run_u += u;
+        }
+      }
+      const uint32_t U = (uint32_t)(tot >> 32);
+      if (tid == 0) sbase[k] = (uint32_t)tot;
+      __syncthreads();  // (B) bucket bases and unit marks are in
+      // -- 3. the bucket of every unit (marks carry bucket + 1 at a bucket's
+      //    first unit; an inclusive max-scan fills the rest), and the sub-tile
+      //    counting-sorted by bucket into shared memory
+      {
+        const uint32_t upt = (U + NT - 1) / NT;
+        const uint32_t u0 = min(tid * upt, U), u1 = min(u0 + upt, U);
+        uint32_t m = 0;
+        for (uint32_t u = u0; u < u1; ++u) m = max(m, (uint32_t)unit_b[u]);
+        uint32_t run = block_excl_max_u32<NT>(m, max_sm);
+        for (uint32_t u = u0; u < u1; ++u) {
+          run = max(run, (uint32_t)unit_b[u]);
+          unit_b[u] = (uint16_t)run;
+        }
+      }
+      const uint32_t pos0 = (uint32_t)(cs + s * ST - sg.start) + q0;  // implicit positions
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        const uint32_t b = bid[r];
+        if (b != 0xffffffffu) {
+          const uint32_t q = sbase[b] + my_cnt[b] + lrank[r];
+          skey[q] = conv_key(key[r], conv);
+          sidx[q] = HAS_IDX ? idx[r] : pos0 + r * 32;
+        }
+      }
+      __syncthreads();  // (C) the sorted sub-tile and the unit buckets are in
+      // -- 4. whole units out: 8 consecutive lanes store one unit (slots
+      //    before the carry count come from the carry area, phantoms are
+      //    skipped)
+      for (uint32_t e = tid; e < U * kUnit; e += NT) {
+        const uint32_t u = e / kUnit, j = e % kUnit;
+        const uint32_t b = (uint32_t)unit_b[u] - 1;
+        const uint32_t m = meta[b], ob = obase[b];
+        const uint32_t cb = (m >> 24) & 7u, ph = m >> 27;
+        const uint32_t v = kUnit * (u - ((m >> 13) & 0x7ffu)) + j;  // slot in the bucket's run
+        const uint32_t q = (m & 0x1fffu) - kUnit + v;                // sorted slot (if not carried)
+        uint64_t kv;
+        uint32_t iv;
+        if (v < cb) {
+          kv = ckey[b * kCarry + v];
+          iv = cidx[b * kCarry + v];
+        } else {
+          kv = skey[q];
+          iv = sidx[q];
+        }
+        if (v >= ph) {
+          dst.key[ob + v] = kv;
+          dst.idx[ob + v] = iv;
+        }
+      }
+      __syncthreads();  // (D) carry slots are read
+      // -- 5. the incomplete last unit of every bucket becomes its carry;
+      //    the unit marks are cleared for the next sub-tile
+      //    (buckets interleaved over the threads, so that neighbouring lanes
+      //    touch neighbouring carry rows; copies unrolled and predicated)
+      for (uint32_t b = tid; b < k; b += NT) {
+        const uint32_t m = meta[b];
+        const uint32_t cb = (m >> 24) & 7u;
+        const uint32_t qb = (m & 0x1fffu) - kUnit;  // sorted slot of run slot 0
+        const uint32_t L = cb + (sbase[b + 1] - sbase[b]), u = L / kUnit, nc = L % kUnit;
+        // run slots [first, L) become carry slots [first - shift, L - shift)
+        const uint32_t first = u == 0 ? cb : kUnit * u;
+        const uint32_t shift = kUnit * u;
+        {
+          uint64_t ck[kCarry];
+#pragma unroll
+          for (int j = 0; j < kCarry; ++j)
+            if (first + j < L) ck[j] = skey[qb + first + j];
+#pragma unroll
+          for (int j = 0; j < kCarry; ++j)
+            if (first + j < L) ckey[b * kCarry + first + j - shift] = ck[j];
+        }
+        {
+          uint32_t ci[kCarry];
+#pragma unroll
+          for (int j = 0; j < kCarry; ++j)
+            if (first + j < L) ci[j] = sidx[qb + first + j];
+#pragma unroll
+          for (int j = 0; j < kCarry; ++j)
+            if (first + j < L) cidx[b * kCarry + first + j - shift] = ci[j];
+        }
+        const uint32_t ph = u == 0 ? (m >> 27) : 0u;
+        obase[b] += shift;
+        meta[b] = (nc << 24) | (ph << 27);
+      }
+      for (uint32_t u = tid; u < U; u += NT) unit_b[u] = 0;
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        key[r] = nkey[r];
+        if (HAS_IDX) idx[r] = nidx[r];
+        bid[r] = nbid[r];
+      }
+    }
+    // the chunk's last, incomplete unit of every bucket (the rest of its
+    // sectors belongs to the next chunk's range)
+    for (uint32_t b = tid; b < k; b += NT) {
+      const uint32_t m = meta[b], ob = obase[b];
+      const uint32_t cb = (m >> 24) & 7u, ph = m >> 27;
+      for (uint32_t j = ph; j < cb; ++j) {
+        dst.key[ob + j] = ckey[b * kCarry + j];
+        dst.idx[ob + j] = cidx[b * kCarry + j];
+      }
+    }
+  }
+}
+
+// Dynamic shared memory limit of the unit scatter (0 until set or if refused).
+size_t g_us_smem_max = 0;
+
+}  // namespace
+
+size_t classify_ids_smem_bytes(uint32_t kmax, int mode) {
+  const size_t Kp = next_pow2_u32(kmax);
+  size_t b = (mode & 1) == 0 ? Kp * 8 : ((size_t)4 << table_bits_for((uint32_t)Kp));
+  b += (size_t)kmax * (8 + 4 + 4 + 2);
+  return (b + 15) & ~(size_t)15;
+}
+
+bool unit_scatter_fits(uint32_t kmax) {
+  return kmax <= (uint32_t)kUnitMaxK && us_smem_bytes(kmax) <= g_us_smem_max;
+}
+
+void set_unit_scatter_attributes() {
+  cudaFuncSetAttribute(k_classify_ids<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)umax64(classify_ids_smem_bytes(kMaxK, 0),
+                                   classify_ids_smem_bytes(kMaxK, 1)));
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  size_t limit = 0;
+  if (cudaFuncGetAttributes(&fa, k_scatter_units<kUsThreads, true>) == cudaSuccess &&
+      (size_t)optin > fa.sharedSizeBytes) {
+    limit = (size_t)optin - fa.sharedSizeBytes;
+    if (limit > us_smem_bytes(kUnitMaxK)) limit = us_smem_bytes(kUnitMaxK);
+    if (cudaFuncSetAttribute(k_scatter_units<kUsThreads, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess)
+      limit = 0;
+  }
+  g_us_smem_max = limit;
+  cudaGetLastError();
+}
+
+void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                         const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t* ssi,
+                         uint32_t* hist, uint32_t kmax, int mode, const char* name) {
+  const size_t smem = classify_ids_smem_bytes(kmax, mode);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_ids<256>, 256, smem);
+  if (nb < 1) nb = 1;
+  const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms * nb);
+  // 16-byte pair loads need a 16-byte aligned key array
+  const int vec = ((uintptr_t)src.key & 15) == 0;
+  Scope sc(e, name);
+  k_classify_ids<256><<<(int)(grid ? grid : 1), 256, smem, e.stream>>>(st, segs, src, ssk, ssi,
+                                                                       hist, kmax, mode, vec);
+}
+
+void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                          const LevelSeg* segs, Src src, const uint32_t* hist_scan, Dst dst,
+                          uint32_t kmax, int unmap_out, const char* name) {
+  const int conv = (src.map_f64 && !unmap_out) ? 1 : ((!src.map_f64 && unmap_out) ? 2 : 0);
+  // units start where the output key address is 64-byte aligned
+  const uint32_t aoff = (uint32_t)(((64 - ((uintptr_t)dst.key & 63)) & 63) / 8);
+  const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms);
+  Scope sc(e, name);
+  if (src.idx)
+    k_scatter_units<kUsThreads, true><<<(int)(grid ? grid : 1), kUsThreads, us_smem_bytes(kmax),
+                                        e.stream>>>(st, segs, src, hist_scan, dst, kmax, conv,
+                                                    aoff);
+  else
+    k_scatter_units<kUsThreads, false><<<(int)(grid ? grid : 1), kUsThreads,
+                                         us_smem_bytes(kmax), e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv, aoff);
+}
+
+}  // namespace rsort

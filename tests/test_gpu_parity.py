@@ -275,6 +275,7 @@ CONFIGS = {
     "table_warpdirect": {"classifier": 1, "warp_direct_max_k": 2048},
     "wide_scatter_everywhere": {"classifier": 1, "wide_scatter_k": 2},
     "deep_levels_stable": {"deep_levels_stable": 1},
+    "staged_scatter": {"unit_scatter": 0},
 }
 
 
