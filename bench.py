@@ -31,7 +31,7 @@ P_VIRTUAL = 1024
 WORKLOAD = "Uniform uint64 keys, n=2^28, p=1024 virtual partitions, seed 1"
 METRIC = "GKeys/s"
 CPU_SAMPLE = 1 << 24   # cpu_baseline leg: 3 runs of this many keys
-REF_SAMPLE = 1 << 22   # --impl reference: keys per step
+REF_SAMPLE = 1 << 24   # --impl reference: keys per step (all-core oracle)
 
 # algorithmic HBM bytes per key of each kernel's input (8 B key, 4 B position)
 ALGO_BYTES_PER_KEY = {
@@ -52,9 +52,7 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    "L1.scatter": 34.10,   # 1.0716 GB read + 1.2169 GB write at 2^26 keys
-    "L2.scatter": 25.29,   # 0.9671 + 0.7303 GB
-    "L1.classify": 8.06,   # 0.5370 + 0.0040 GB
+    "L2.scatter": 25.29,   # 0.9671 + 0.7303 GB at 2^26 keys
     "L2.classify": 9.39,   # 0.5519 + 0.0783 GB
 }
 
@@ -160,7 +158,9 @@ def _dist():
 
 
 def run_reference(args):
-    """The CPU oracle as it stands, on bounded samples of the same workload."""
+    """The CPU oracle as it stands, on bounded samples of the same workload,
+    on every host core (its all-core merge sort: nproc chunks sorted by their
+    own threads, then pairwise merges)."""
     import numpy as np
 
     import instances
@@ -172,18 +172,20 @@ def run_reference(args):
     n = args.n
     chunk = min(REF_SAMPLE, max(1, n // 2))
     keys = instances.generate("uniform", n, p=P_VIRTUAL, seed=1)
+    cores = os.cpu_count() or 1
     times = []
     for step in range(args.warmup + args.steps):
         lo = (step * chunk) % max(1, n - chunk)
         sample = np.ascontiguousarray(keys[lo:lo + chunk])
         t0 = time.perf_counter()
-        oracle.sort(sample)
+        oracle.sort_parallel(sample, threads=cores)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
     ms = 1e3 * statistics.mean(times)
     value = chunk / (ms / 1e3) / 1e9
-    sample_desc = (f"{chunk} consecutive keys of the n = {n} Uniform input per step")
+    sample_desc = (f"{chunk} consecutive keys of the n = {n} Uniform input per step, "
+                   f"all-core merge sort on {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -192,7 +194,7 @@ def run_reference(args):
         "config": {"workload": WORKLOAD if n == N_KEYS else
                    f"Uniform uint64 keys, n={n}, p={P_VIRTUAL} virtual partitions, seed 1",
                    "n": n, "p": P_VIRTUAL},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -200,108 +202,214 @@ def run_reference(args):
 
 
 def cpu_baseline_leg():
-    """Oracle timed on the host on a bounded sample (rank 0, N = 1 only)."""
+    """Oracle timed on the host on a bounded sample (rank 0, N = 1 only): the
+    all-core merge sort (nproc equal chunks sorted by their own threads, then
+    pairwise merges) and the single-thread one."""
     import numpy as np
 
     import instances
     import oracle
 
-    sample = instances.generate("uniform", CPU_SAMPLE, p=P_VIRTUAL, seed=1)
+    sample = np.ascontiguousarray(instances.generate("uniform", CPU_SAMPLE, p=P_VIRTUAL, seed=1))
+    cores = os.cpu_count() or 1
     ts = []
     for _ in range(3):
         t0 = time.perf_counter()
-        oracle.sort(np.ascontiguousarray(sample))
+        oracle.sort_parallel(sample, threads=cores)
         ts.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    oracle.sort(sample)
+    t1 = time.perf_counter() - t0
     v = CPU_SAMPLE / statistics.median(ts) / 1e9
-    return {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"first {CPU_SAMPLE} keys of the Uniform instance, 3 runs, median"}
+    return {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE} keys of the Uniform instance; all-core merge sort "
+                      f"({cores} threads), median of 3",
+            "single_core_value": CPU_SAMPLE / t1 / 1e9, "nproc": cores}
 
 
-def batched_leg(ctx, dev, nseg=100_000, maxlog=15, plain_subset=20_000):
-    """Batched segmented sort of float64 segments (log-uniform sizes, 10%
-    duplicates) in one launch sequence, against one plain rsort_sort per
-    segment on a subset of the same segments."""
-    import numpy as np
+def _event_ms(fn, stream, reps):
+    import torch
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def config1_leg(ctx, dev, n=1 << 20, p=64, reps=20):
+    """Plain sort of 2^20 uniform uint64 keys as p = 64 virtual partitions."""
     import torch
 
     import instances
 
-    keys, offs = instances.segmented_f64(nseg, maxlog, seed=1)
-    n = int(keys.shape[0])
-    x = torch.from_numpy(keys.view(np.float64)).to(dev)
-    o = torch.from_numpy(offs.view(np.int64)).to(dev)
+    keys = instances.generate_torch("uniform", n, p=p, seed=1, device=dev)
+    ko = torch.empty_like(keys)
+    po = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    fn = lambda: ctx.sort(keys, p=p, keys_out=ko, perm_out=po)
+    for _ in range(3):
+        fn()
+    ms = _event_ms(fn, stream, reps)
+    return {"workload": f"Uniform uint64 keys, n=2^20, p={p}, seed 1", "ms": ms,
+            "gkeys_s": n / (ms / 1e3) / 1e9}
+
+
+def instances_leg(ctx, dev, n=1 << 28, p=1024, reps=3):
+    """Configs 2 and 3: the full sort on every input instance at 2^28 keys and
+    p = 1024 (Section 6's robustness claim: duplicates, skew and presorted
+    orders should neither unbalance nor slow the sort).  Device time (median
+    of reps after one warm-up), GKeys/s and the level-1 balance (largest
+    virtual partition over the mean n/p)."""
+    import torch
+
+    import instances
+
+    out = {"workload": f"rsort_sort of n=2^{n.bit_length() - 1} u64 keys, p={p}, per instance"}
+    stream = torch.cuda.current_stream(dev)
+    ko = torch.empty(n, dtype=torch.int64, device=dev)
+    po = torch.empty(n, dtype=torch.int32, device=dev)
+    for name in instances.NAMES:
+        keys = instances.generate_torch(name, n, p=p, seed=1, device=dev)
+        _, _, st = ctx.sort(keys, p=p, keys_out=ko, perm_out=po, stats=True)
+        ms = _event_ms(lambda: ctx.sort(keys, p=p, keys_out=ko, perm_out=po), stream, reps)
+        out[name] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9,
+                     "max_over_mean": st.max_over_mean}
+        del keys
+    return out
+
+
+def partition_leg(ctx, dev, n=1 << 26, k=1024, over=10, reps=3):
+    """The partition step alone on duplicate-heavy and unique inputs: the
+    robust step, the NTB ablation (classification by key only) and AMS
+    overpartitioning (b = 10: eps = 0.2 with one level).  Reports device time
+    and the largest partition over the mean n/k."""
+    import torch
+
+    import instances
+
+    out = {"workload": f"one partition step, n=2^{n.bit_length() - 1}, k={k}, seed 1",
+           "variants": {"robust": "tie_break=1, b=1", "ntb": "tie_break=0, b=1",
+                        f"over{over}": f"tie_break=1, b={over}"}}
+    stream = torch.cuda.current_stream(dev)
+    for name in ("uniform", "zero", "deter_dupl", "rand_dupl"):
+        keys = instances.generate_torch(name, n, p=k, seed=1, device=dev)
+        row = {}
+        for label, kw in (("robust", {}), ("ntb", {"tie_break": False}),
+                          (f"over{over}", {"overpartition": over})):
+            res = ctx.partition_ex(keys, k, seed=1, **kw)
+            ms = _event_ms(lambda: ctx.partition_ex(keys, k, seed=1, **kw), stream, reps)
+            sizes = torch.diff(res[2]).max().item()
+            row[label] = {"ms": ms, "max_over_mean": sizes / (n / k)}
+            del res
+        out[name] = row
+        del keys
+        torch.cuda.empty_cache()
+    return out
+
+
+def autotune_leg(dev, path):
+    """Runs the autotuner on this GPU and writes its table (bounded: about
+    a dozen seconds)."""
+    from paper_1606_08766_gb300 import autotune
+
+    t0 = time.perf_counter()
+    r = autotune.tune(dev.index, keys_per_class=1 << 24, reps=3)
+    autotune.write_table(r, path)
+    return {"seconds": time.perf_counter() - t0, "table": r.table(),
+            "mixed_default_ms": r.default_ms, "mixed_tuned_ms": r.tuned_ms,
+            "reverted_to_defaults": r.reverted,
+            "knobs": {k.name: {"chosen": k.chosen, "default": k.default,
+                               "ms": {str(v): round(t, 4) for v, t in k.ms.items()}}
+                      for k in r.knobs}}
+
+
+def batched_leg(ctx, tuned, dev, nseg, maxlog, total_cap=None, plain_max=20_000, label=""):
+    """Batched segmented sort of float64 segments (log-uniform sizes, 10%
+    duplicates) in one launch sequence with the default plan and with the
+    autotuned one, replayed from a CUDA graph, against one plain rsort_sort
+    per segment (all segments, or the first plain_max)."""
+    import torch
+
+    import instances
+
+    x, o = instances.segmented_f64_torch(nseg, maxlog, seed=1, total_cap=total_cap, device=dev)
+    n = int(x.numel())
+    nsegs = int(o.numel() - 1)
     ko = torch.empty_like(x)
     po = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(2):
-        ctx.segmented(x, o, keys_out=ko, perm_out=po)
-    torch.cuda.synchronize(dev)
-    reps = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        ctx.segmented(x, o, keys_out=ko, perm_out=po)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_batched = e0.elapsed_time(e1) / reps
-    # the same launch sequence captured once in a CUDA graph and replayed
+    res = {}
+    for name, c in (("default", ctx), ("tuned", tuned)):
+        for _ in range(2):
+            c.segmented(x, o, keys_out=ko, perm_out=po)
+        res[name] = _event_ms(lambda: c.segmented(x, o, keys_out=ko, perm_out=po), stream, 3)
+    # the tuned launch sequence captured once in a CUDA graph and replayed
     side = torch.cuda.Stream(dev)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(side):
-        ctx.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
+        tuned.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
     torch.cuda.synchronize(dev)
     with torch.cuda.graph(g, stream=side):
-        ctx.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
+        tuned.segmented(x, o, keys_out=ko, perm_out=po, stream=side)
     g.replay()
     torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(reps):
-        g.replay()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_graph = e0.elapsed_time(e1) / reps
+    ms_graph = _event_ms(g.replay, stream, 3)
     # one plain sort per segment (pointer-level calls, same stream)
-    m = int(offs[plain_subset])
+    offs_l = o.cpu().tolist()
+    nplain = min(plain_max, nsegs)
+    m = offs_l[nplain]
     ko2 = torch.empty(m, dtype=torch.float64, device=dev)
     po2 = torch.empty(m, dtype=torch.int32, device=dev)
     xp, kp, pp, sh = x.data_ptr(), ko2.data_ptr(), po2.data_ptr(), stream.cuda_stream
-    offs_l = [int(v) for v in offs[: plain_subset + 1]]
 
     def plain_pass():
-        for s in range(plain_subset):
+        for s in range(nplain):
             a, b = offs_l[s], offs_l[s + 1]
             ctx.sort_raw(1, xp + 8 * a, kp + 8 * a, pp + 4 * a, b - a, 1, 1, sh)
 
     plain_pass()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     plain_pass()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_plain = e0.elapsed_time(e1)
     wall_plain = time.perf_counter() - t0
+    tuned.segmented(x, o, keys_out=ko, perm_out=po)
     same = bool(torch.equal(ko2, ko[:m])) and bool(torch.equal(po2, po[:m]))
     gk = lambda keys_, ms_: keys_ / (ms_ / 1e3) / 1e9
     plain_gk = m / max(wall_plain, ms_plain / 1e3) / 1e9
-    return {"workload": f"{offs.shape[0] - 1} float64 segments, sizes floor(exp(U ln 2^{maxlog})), "
+    return {"workload": f"{label}{nsegs} float64 segments, sizes floor(exp(U ln 2^{maxlog})), "
                         f"10% duplicates, {n} keys",
-            "keys": n, "segments": int(offs.shape[0] - 1),
-            "batched_gkeys_s": gk(n, ms_batched), "batched_ms": ms_batched,
+            "keys": n, "segments": nsegs,
+            "default_gkeys_s": gk(n, res["default"]), "default_ms": res["default"],
+            "tuned_gkeys_s": gk(n, res["tuned"]), "tuned_ms": res["tuned"],
+            "tuned_over_default": res["default"] / res["tuned"],
             "graph_replay_gkeys_s": gk(n, ms_graph),
             "plain_per_segment_gkeys_s": plain_gk,
-            "plain_subset": f"first {plain_subset} segments ({m} keys), one rsort_sort each",
-            "speedup_vs_plain": gk(n, ms_batched) / plain_gk,
+            "plain_subset": f"first {nplain} segments ({m} keys), one rsort_sort each",
+            "speedup_vs_plain": gk(n, res["tuned"]) / plain_gk,
             "identical_to_plain": same}
 
 
-def serving_leg(dev, requests=2000, lo_log2=4, hi_log2=20, seed=5):
-    """Continuous batching under the serving runtime against serial plain
-    sorts of the same requests, plus latency under Poisson arrivals."""
+def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95, 1.2),
+                budget=64 << 30, seed=5):
+    """Config 5: a stream of sort requests with sizes log-uniform in
+    [2^lo, 2^hi], u64 or f64 keys (50/50), each drawing one of the 11
+    instances, p_virtual = min(1024, ceil(n / 2^8)), served by continuous
+    batching under an HBM budget, against serial plain sorts of the same
+    requests.  Capacity = everything offered at once; then Poisson arrivals
+    at the given fractions of that capacity, each with p50 / p99 latency."""
     import math
     import random
 
-    import numpy as np
     import torch
 
     import instances
@@ -312,135 +420,75 @@ def serving_leg(dev, requests=2000, lo_log2=4, hi_log2=20, seed=5):
              for _ in range(requests)]
     reqs = []
     for i, n in enumerate(sizes):
-        name = instances.NAMES[i % len(instances.NAMES)]
-        k = instances.generate(name, n, p=16, seed=seed + i)
-        if i % 2:
-            t = torch.from_numpy(k.view(np.int64)).to(dev)
-            kt = 0
+        name = instances.NAMES[rng.randrange(len(instances.NAMES))]
+        p = min(1024, -(-n // 256))
+        k = instances.generate_torch(name, n, p=max(p, 1), seed=seed + i, device=dev)
+        if rng.random() < 0.5:
+            t, kt = k, 0
         else:
-            t = torch.from_numpy(k.astype(np.float64) - 2.0 ** 63).to(dev)
-            kt = 1
-        reqs.append((t, torch.empty_like(t), torch.empty(n, dtype=torch.int32, device=dev), kt))
+            t, kt = k.to(torch.float64), 1
+        reqs.append((t, torch.empty_like(t), torch.empty(n, dtype=torch.int32, device=dev), kt, p))
     total = sum(sizes)
     torch.cuda.synchronize(dev)
-    ctx = Context(dev.index)
-    # warm-up: every request once through the server
-    ts = [ctx.submit(t, o, p, key_type=kt) for t, o, p, kt in reqs]
-    for t in ts:
-        ctx.wait(t, 300)
+    ctx = Context(dev.index, hbm_budget_bytes=budget)
+
+    def offer_all():
+        t0 = time.perf_counter()
+        ts = [ctx.submit(t, o, pm, p=p, key_type=kt) for t, o, pm, kt, p in reqs]
+        for t in ts:
+            assert ctx.wait(t, 300) == 0
+        return time.perf_counter() - t0
+
+    offer_all()                        # warm-up: every request once through the server
     ctx.reset_serve_stats()
-    # capacity: everything offered at once
-    t0 = time.perf_counter()
-    ts = [ctx.submit(t, o, p, key_type=kt) for t, o, p, kt in reqs]
-    for t in ts:
-        assert ctx.wait(t, 300) == 0
-    wall = time.perf_counter() - t0
+    wall = offer_all()
     sat = ctx.serve_stats()
     # serial plain sorts, one rsort_sort per request on one stream
     stream = torch.cuda.current_stream(dev)
     plain = Context(dev.index)
-    for t, o, p, kt in reqs[:50]:
-        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), p.data_ptr(), t.numel(), 1, 1,
+    for t, o, pm, kt, p in reqs[:50]:
+        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), pm.data_ptr(), t.numel(), p, 1,
                        stream.cuda_stream)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for t, o, p, kt in reqs:
-        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), p.data_ptr(), t.numel(), 1, 1,
+    for t, o, pm, kt, p in reqs:
+        plain.sort_raw(kt, t.data_ptr(), o.data_ptr(), pm.data_ptr(), t.numel(), p, 1,
                        stream.cuda_stream)
     torch.cuda.synchronize(dev)
     wall_plain = time.perf_counter() - t0
     plain.close()
-    # latency under Poisson arrivals at half the measured capacity
-    rate = 0.5 * requests / wall
-    ctx.reset_serve_stats()
-    ts = []
-    t_next = time.perf_counter()
-    for t, o, p, kt in reqs:
-        t_next += rng.expovariate(rate)
-        while time.perf_counter() < t_next:
-            pass
-        ts.append(ctx.submit(t, o, p, key_type=kt))
-    for t in ts:
-        assert ctx.wait(t, 300) == 0
-    poi = ctx.serve_stats()
-    ctx.close()
-    return {"workload": f"{requests} requests, sizes log-uniform in [2^{lo_log2}, 2^{hi_log2}], "
-                        f"u64/f64 alternating over the 11 instances, {total} keys",
-            "served_requests_s": requests / wall, "served_gkeys_s": total / wall / 1e9,
-            "plain_serial_requests_s": requests / wall_plain,
-            "plain_serial_gkeys_s": total / wall_plain / 1e9,
-            "speedup_vs_plain": wall_plain / wall,
-            "saturated_p50_us": sat["p50_us"], "saturated_p99_us": sat["p99_us"],
-            "mean_batch_requests": sat["mean_batch_requests"],
-            "poisson_rate_requests_s": rate, "p50_us": poi["p50_us"], "p99_us": poi["p99_us"]}
-
-
-def instances_leg(ctx, dev, n=1 << 26, p=1024, reps=3):
-    """The full sort on every input instance (Section 6's robustness claim:
-    duplicates, skew and presorted orders should not slow the sort down).
-    Device time per sort (median of reps after one warm-up) and GKeys/s."""
-    import numpy as np
-    import torch
-
-    import instances
-
-    out = {"workload": f"rsort_sort of n=2^{n.bit_length() - 1} u64 keys, p={p}, per instance"}
-    stream = torch.cuda.current_stream(dev)
-    ko = torch.empty(n, dtype=torch.int64, device=dev)
-    po = torch.empty(n, dtype=torch.int32, device=dev)
-    for name in instances.NAMES:
-        keys = torch.from_numpy(instances.generate(name, n, p=p, seed=1).view(np.int64)).to(dev)
-        ctx.sort(keys, p=p, keys_out=ko, perm_out=po)
+    cap_rate = requests / wall
+    out = {"workload": f"{requests} requests (of the 200,000 of the stated stream), sizes "
+                       f"log-uniform in [2^{lo_log2}, 2^{hi_log2}], u64/f64 50/50, a random "
+                       f"instance each, p_virtual = min(1024, ceil(n/2^8)), {total} keys, "
+                       f"HBM budget {budget >> 30} GiB",
+           "capacity_requests_s": cap_rate, "served_gkeys_s": total / wall / 1e9,
+           "plain_serial_requests_s": requests / wall_plain,
+           "plain_serial_gkeys_s": total / wall_plain / 1e9,
+           "speedup_vs_plain": wall_plain / wall,
+           "saturated_p50_us": sat["p50_us"], "saturated_p99_us": sat["p99_us"],
+           "mean_batch_requests": sat["mean_batch_requests"], "loads": {}}
+    for load in loads:
+        rate = load * cap_rate
+        ctx.reset_serve_stats()
         ts = []
-        for _ in range(reps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctx.sort(keys, p=p, keys_out=ko, perm_out=po)
-            b.record(stream)
-            torch.cuda.synchronize(dev)
-            ts.append(a.elapsed_time(b))
-        ms = sorted(ts)[len(ts) // 2]
-        out[name] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9}
-        del keys
-    return out
-
-
-def partition_leg(ctx, dev, n=1 << 26, k=1024, over=10, reps=3):
-    """The partition step alone on duplicate-heavy and unique inputs: the
-    robust step, the NTB ablation (classification by key only) and AMS
-    overpartitioning (b = 10: eps = 0.2 with one level).  Reports device time
-    and the largest partition over the mean n/k."""
-    import numpy as np
-    import torch
-
-    import instances
-
-    out = {"workload": f"one partition step, n=2^{n.bit_length() - 1}, k={k}, seed 1",
-           "variants": {"robust": "tie_break=1, b=1", "ntb": "tie_break=0, b=1",
-                        f"over{over}": f"tie_break=1, b={over}"}}
-    stream = torch.cuda.current_stream(dev)
-    for name in ("uniform", "zero", "deter_dupl", "rand_dupl"):
-        keys = torch.from_numpy(instances.generate(name, n, p=k, seed=1).view(np.int64)).to(dev)
-        row = {}
-        for label, kw in (("robust", {}), ("ntb", {"tie_break": False}),
-                          (f"over{over}", {"overpartition": over})):
-            ctx.partition_ex(keys, k, seed=1, **kw)
-            ts = []
-            for _ in range(reps):
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                res = ctx.partition_ex(keys, k, seed=1, **kw)
-                b.record(stream)
-                torch.cuda.synchronize(dev)
-                ts.append(a.elapsed_time(b))
-            sizes = torch.diff(res[2]).max().item()
-            row[label] = {"ms": sorted(ts)[len(ts) // 2], "max_over_mean": sizes / (n / k)}
-            del res
-        out[name] = row
-        del keys
-        torch.cuda.empty_cache()
+        t_start = time.perf_counter()
+        t_next = t_start
+        for t, o, pm, kt, p in reqs:
+            t_next += rng.expovariate(rate)
+            while time.perf_counter() < t_next:
+                pass
+            ts.append(ctx.submit(t, o, pm, p=p, key_type=kt))
+        for t in ts:
+            assert ctx.wait(t, 300) == 0
+        el = time.perf_counter() - t_start
+        st = ctx.serve_stats()
+        out["loads"][str(load)] = {"offered_requests_s": rate, "served_requests_s": requests / el,
+                                   "served_gkeys_s": total / el / 1e9, "p50_us": st["p50_us"],
+                                   "p99_us": st["p99_us"], "max_us": st["max_us"]}
+    ctx.close()
+    del reqs
+    torch.cuda.empty_cache()
     return out
 
 
@@ -611,11 +659,23 @@ def run_rsort(args):
     cpu = cpu_baseline_leg() if (rank == 0 and ws == 1) else None
     extra = {}
     if rank == 0 and ws == 1 and not args.skip_systems:
-        del keys_pin
+        import tempfile
+
+        from paper_1606_08766_gb300 import Context as _Ctx
+        del keys_pin, keys, keys_out, perm
         torch.cuda.empty_cache()
+        extra["config1"] = config1_leg(ctx, dev)
         extra["instances"] = instances_leg(ctx, dev)
+        torch.cuda.empty_cache()
         extra["partition_variants"] = partition_leg(ctx, dev)
-        extra["batched"] = batched_leg(ctx, dev)
+        table = os.path.join(tempfile.mkdtemp(), "gb300.tune")
+        extra["autotune"] = autotune_leg(dev, table)
+        tuned = _Ctx(local, tune_table=table)
+        extra["batched"] = {
+            "4a": batched_leg(ctx, tuned, dev, 100_000, 15, label="config 4a: "),
+            "4b": batched_leg(ctx, tuned, dev, 100_000, 20, total_cap=N_KEYS,
+                              label="config 4b: ")}
+        tuned.close()
         torch.cuda.empty_cache()
         extra["serving"] = serving_leg(dev)
     if rank == 0:

@@ -326,10 +326,28 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                above 4096 keys after the last level is merge-sorted
  *                through global memory by one CTA (slow; with 3 levels the
  *                sampling makes it vanishingly rare below 2^31 keys).
- *   medium_sort  buckets of 1025..4096 keys: 0 (default) equal-width bins and
- *                rank-by-counting; 1 in-SM quicksort whose pivots are the
- *                binary-tree median approximation (see rsort_approx_median)
- *                of a 256-element stratified sample of each segment.
+ *   The in-SM sort of a bucket is chosen by its size (Section 6's
+ *   size-dependent choice, applied per bucket; paper_1606_08766_gb300.autotune
+ *   measures these on the device and writes a table of them):
+ *   small_cap, mid_cap  buckets of at most small_cap keys (64..1024, default
+ *                1024) are sorted by 128-thread CTAs, of at most mid_cap
+ *                (64..2048, default 2048) by 256-thread CTAs, larger ones (up
+ *                to 4096) by 512-thread CTAs.
+ *   rank_max     buckets of at most this many keys (0..128, default 64) are
+ *                sorted by rank-by-counting (Appendix "Fast Work-Inefficient
+ *                Ranking").
+ *   sort_small, sort_mid, sort_medium  the algorithm of each of the three
+ *                classes above: 0 (default) equal-width bins with ranking
+ *                inside the bins (bitonic when keys cluster), 2 bitonic sort
+ *                (Appendix "Bitonic Sort"), and for the mid and medium
+ *                classes 1: in-SM quicksort whose pivots are the binary-tree
+ *                median approximation (see rsort_approx_median) of a
+ *                256-element stratified sample of each segment.
+ *   medium_sort  1 sets sort_mid and sort_medium to quicksort, 0 to bins.
+ *   target_bucket@c  (c = 1..32) the fan-out target of segments of
+ *                ceil(log2 m) = c keys (64..4096; 0 falls back to
+ *                target_bucket): the bucket count of such a segment is
+ *                ceil(m / target).
  *   unit_scatter  1 (default): a level that keeps input order inside buckets
  *                (level 1, the partition step) and has at most 1024 buckets
  *                stores every element's bucket id when it classifies, and

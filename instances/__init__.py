@@ -390,3 +390,61 @@ def generate_torch(name: str, n: int, p: int = 1024, seed: int = 1, g: int = 32,
         return table[_t_partition_of(e, n, p)]
 
     raise AssertionError(name)
+
+
+def _t_umod_t(r, m):
+    """r (int64 holding uint64 patterns) modulo the int64 tensor m (0 < m < 2**62)."""
+    import torch
+    a = torch.remainder(r, m)
+    c63 = torch.remainder(torch.remainder(torch.full_like(m, (1 << 63) - 1), m) + 1, m)
+    c64 = torch.remainder(2 * c63, m)           # 2**64 mod m
+    return torch.where(r < 0, torch.remainder(a + c64, m), a)
+
+
+def segmented_f64_torch(num_segments: int, max_log2: int, seed: int = 1, dup_frac: float = 0.1,
+                        total_cap: int | None = None, device="cpu"):
+    """segmented_f64 drawn with torch on ``device``: the same segment sizes and
+    duplicate choices, keys equal to the numpy ones up to the last bits of the
+    device's log / sqrt / cos.  Returns (keys as float64 tensor, int64
+    offsets tensor)."""
+    import torch
+    st = _stream(seed, "segmented_f64")
+    ru = splitmix64(st, np.arange(num_segments, dtype=U64))
+    u = (ru >> U64(11)).astype(np.float64) * 2.0 ** -53
+    sizes = np.floor(np.exp(u * (max_log2 * math.log(2.0)))).astype(np.int64)
+    sizes = np.clip(sizes, 1, (1 << max_log2))
+    if total_cap is not None:
+        cum = np.cumsum(sizes)
+        sizes = sizes[cum <= total_cap]
+    offsets = np.zeros(sizes.shape[0] + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    n = int(offsets[-1])
+    dev = torch.device(device)
+    base = num_segments * 4
+    keys = torch.empty(n, dtype=torch.float64, device=dev)
+    chunk = 1 << 24
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        e = torch.arange(lo, hi, dtype=torch.int64, device=dev)
+        r1 = t_splitmix64(st, base + 4 * e)
+        r2 = t_splitmix64(st, base + 4 * e + 1)
+        u1 = (_t_shr(r1, 11).to(torch.float64) + 1.0) * 2.0 ** -53
+        u2 = _t_shr(r2, 11).to(torch.float64) * 2.0 ** -53
+        keys[lo:hi] = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+    offs = torch.from_numpy(offsets).to(dev)
+    if dup_frac > 0 and n:
+        sz = torch.from_numpy(sizes).to(dev)
+        picked, sources = [], []
+        for lo in range(0, n, chunk):
+            hi = min(n, lo + chunk)
+            e = torch.arange(lo, hi, dtype=torch.int64, device=dev)
+            seg = torch.searchsorted(offs, e, right=True) - 1
+            rsel = t_splitmix64(st, base + 4 * e + 2)
+            rsrc = t_splitmix64(st, base + 4 * e + 3)
+            pick = _t_shr(rsel, 11).to(torch.float64) * 2.0 ** -53 < dup_frac
+            src = offs[seg] + _t_umod_t(rsrc, sz[seg])
+            picked.append(e[pick])
+            sources.append(src[pick])
+        idx, src = torch.cat(picked), torch.cat(sources)
+        keys[idx] = keys[src]
+    return keys, offs

@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp],
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp],
                    check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -51,6 +51,9 @@ def _load():
             u32p = ctypes.POINTER(ctypes.c_uint32)
             lib.oracle_sort.argtypes = [u64p, ctypes.c_uint64, ctypes.c_int, u64p, u32p]
             lib.oracle_sort.restype = ctypes.c_int
+            lib.oracle_sort_parallel.argtypes = [u64p, ctypes.c_uint64, ctypes.c_int,
+                                                 ctypes.c_int, u64p, u32p]
+            lib.oracle_sort_parallel.restype = ctypes.c_int
             lib.oracle_segmented.argtypes = [u64p, u64p, ctypes.c_uint32, ctypes.c_int,
                                              u64p, u32p]
             lib.oracle_segmented.restype = ctypes.c_int
@@ -99,6 +102,20 @@ def sort(keys, key_type: int = KEY_U64):
     rc = _load().oracle_sort(_p64(k), n, key_type, _p64(ko), _p32(po))
     if rc:
         raise ValueError("oracle_sort rejected its arguments")
+    return ko, po
+
+
+def sort_parallel(keys, key_type: int = KEY_U64, threads: int | None = None):
+    """sort() on `threads` host threads (default: every core): equal chunks
+    merge-sorted at once, then pairwise merges."""
+    k = _as_bits(keys)
+    n = k.shape[0]
+    t = threads or os.cpu_count() or 1
+    ko = np.empty(n, np.uint64)
+    po = np.empty(n, np.uint32)
+    rc = _load().oracle_sort_parallel(_p64(k), n, key_type, int(t), _p64(ko), _p32(po))
+    if rc:
+        raise ValueError("oracle_sort_parallel rejected its arguments")
     return ko, po
 
 

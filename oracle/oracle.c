@@ -18,6 +18,11 @@
  *                      positions are distinct the result is unique:
  *                      perm is the permutation with (phi(x[perm[j]]), perm[j])
  *                      strictly increasing in j.  Textbook top-down merge sort.
+ *   oracle_sort_parallel  The same result on several host threads: the index
+ *                      array is cut into equal chunks that the threads
+ *                      merge-sort at once, then adjacent sorted runs are
+ *                      merged pairwise, the merges of a round running at
+ *                      once.  Used to time the oracle on all host cores.
  *   oracle_segmented   The same contract applied to each segment on its own
  *                      (segment-local positions).
  *   oracle_partition   One level of the robust sample-sort partition step
@@ -75,6 +80,7 @@
  *
  * parity pins: see tests/test_oracle_pins.py.  All functions are pinned.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -161,6 +167,122 @@ int oracle_sort(const uint64_t *keys_bits, uint64_t n, int key_type,
     free(key);
     free(scratch);
     return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* The same merge sort on several threads                                  */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t *idx, *scratch;
+    const uint64_t *key;
+    uint64_t lo, mid, hi;   /* chunk [lo, hi), or runs [lo, mid) and [mid, hi) */
+} par_task;
+
+static void *sort_chunk(void *arg)
+{
+    par_task *t = (par_task *)arg;
+    merge_sort(t->idx, t->scratch, t->lo, t->hi, t->key);
+    return NULL;
+}
+
+/* Merges the sorted runs idx[lo, mid) and idx[mid, hi) into scratch[lo, hi). */
+static void *merge_runs(void *arg)
+{
+    par_task *t = (par_task *)arg;
+    uint64_t i = t->lo, j = t->mid, o = t->lo;
+    while (i < t->mid && j < t->hi) {
+        uint32_t a = t->idx[i], b = t->idx[j];
+        if (pair_less(t->key[b], b, t->key[a], a))
+            t->scratch[o++] = t->idx[j++];
+        else
+            t->scratch[o++] = t->idx[i++];
+    }
+    while (i < t->mid)
+        t->scratch[o++] = t->idx[i++];
+    while (j < t->hi)
+        t->scratch[o++] = t->idx[j++];
+    return NULL;
+}
+
+/* oracle_sort's result computed by nthreads threads (1..256): chunk c of the
+ * positions is [c*n/T, (c+1)*n/T); each is merge-sorted by its own thread, then
+ * every round merges runs 2r and 2r+1 (one thread per merge) until one run is
+ * left.  Returns 0, or -1 on bad arguments / allocation or thread failure. */
+int oracle_sort_parallel(const uint64_t *keys_bits, uint64_t n, int key_type, int nthreads,
+                         uint64_t *keys_out, uint32_t *perm_out)
+{
+    if (n > 0xFFFFFFFFULL || (key_type != 0 && key_type != 1) || nthreads < 1 ||
+        nthreads > 256)
+        return -1;
+    if (n == 0)
+        return 0;
+    uint64_t T = (uint64_t)nthreads < n ? (uint64_t)nthreads : n;
+    uint64_t *key = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint32_t *scratch = (uint32_t *)malloc(n * sizeof(uint32_t));
+    uint64_t *bound = (uint64_t *)malloc((T + 1) * sizeof(uint64_t));
+    par_task *task = (par_task *)malloc(T * sizeof(par_task));
+    pthread_t *th = (pthread_t *)malloc(T * sizeof(pthread_t));
+    int rc = -1;
+    if (!key || !scratch || !bound || !task || !th)
+        goto done;
+    for (uint64_t i = 0; i < n; ++i) {
+        key[i] = phi(keys_bits[i], key_type);
+        perm_out[i] = (uint32_t)i;
+    }
+    for (uint64_t c = 0; c <= T; ++c)
+        bound[c] = c * n / T;
+    for (uint64_t c = 0; c < T; ++c) {
+        task[c] = (par_task){perm_out, scratch, key, bound[c], bound[c], bound[c + 1]};
+        if (pthread_create(&th[c], NULL, sort_chunk, &task[c]) != 0) {
+            for (uint64_t d = 0; d < c; ++d)
+                pthread_join(th[d], NULL);
+            goto done;
+        }
+    }
+    for (uint64_t c = 0; c < T; ++c)
+        pthread_join(th[c], NULL);
+    /* pairwise merges: runs are bound[0..runs]; each round halves the runs */
+    uint32_t *src = perm_out, *dst = scratch;
+    uint64_t runs = T;
+    while (runs > 1) {
+        uint64_t pairs = runs / 2, started = 0;
+        for (uint64_t r = 0; r < pairs; ++r) {
+            task[r] = (par_task){src, dst, key, bound[2 * r], bound[2 * r + 1],
+                                 bound[2 * r + 2]};
+            if (pthread_create(&th[r], NULL, merge_runs, &task[r]) != 0)
+                break;
+            ++started;
+        }
+        for (uint64_t r = 0; r < started; ++r)
+            pthread_join(th[r], NULL);
+        if (started < pairs)
+            goto done;
+        if (runs % 2)   /* the odd run out is carried over unchanged */
+            memcpy(dst + bound[runs - 1], src + bound[runs - 1],
+                   (size_t)(bound[runs] - bound[runs - 1]) * sizeof(uint32_t));
+        /* run r of the next round starts where run 2r started (the carried
+         * odd run included); the last bound stays n */
+        for (uint64_t r = 0; r <= pairs; ++r)
+            bound[r] = bound[2 * r];
+        runs = pairs + (runs % 2);
+        bound[runs] = n;
+        uint32_t *t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != perm_out)
+        memcpy(perm_out, src, (size_t)n * sizeof(uint32_t));
+    for (uint64_t j = 0; j < n; ++j)
+        keys_out[j] = keys_bits[perm_out[j]];
+    rc = 0;
+done:
+    free(key);
+    free(scratch);
+    free(bound);
+    free(task);
+    free(th);
+    return rc;
 }
 
 /* The same contract applied to every segment [offsets[s], offsets[s+1]) on its

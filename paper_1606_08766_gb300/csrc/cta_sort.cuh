@@ -90,19 +90,38 @@ __device__ __forceinline__ void count_algo(uint64_t* algo, int which, uint32_t m
   if (algo && threadIdx.x == 0) atomicAdd((unsigned long long*)&algo[which], (unsigned long long)m);
 }
 
+// Bitonic sort of the whole bucket (Appendix "Bitonic Sort"): pairs padded to
+// a power of two with (UINT64_MAX, UINT32_MAX), ordered by (key, position).
+template <int NT, int ITEMS>
+__device__ __forceinline__ void cta_bitonic_pairs(const uint64_t (&key)[ITEMS],
+                                                  const uint32_t (&idx)[ITEMS], uint32_t m,
+                                                  const CtaSortSmem& s) {
+  const uint32_t P = next_pow2_u32(m);
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const uint32_t e = r * NT + threadIdx.x;
+    if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
+  }
+  for (uint32_t e = m + threadIdx.x; e < P; e += NT) { s.k[e] = ~0ULL; s.i[e] = ~0u; }
+  block_bitonic_sort<NT>(s.k, s.i, (int)P);
+}
+
 // Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
 // in_position_order() says whether the elements arrive with increasing
 // positions; it is asked only when all keys are equal.  algo (nullable) gets
 // m added to the counter of the branch taken (kAlgoRank, kAlgoInOrder,
-// kAlgoBitonic or kAlgoBins).
+// kAlgoBitonic or kAlgoBins).  rank_max bounds rank-by-counting (at most NT
+// elements: one per thread); force_bitonic sorts every larger bucket by
+// bitonic sort instead of the bins.
 template <int NT, int ITEMS, typename InOrderFn>
 __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], uint32_t m,
                                InOrderFn in_position_order, const CtaSortSmem& s, uint64_t* red,
-                               uint64_t* scan_sm, uint64_t* algo) {
+                               uint64_t* scan_sm, uint64_t* algo, uint32_t rank_max = kRankMax,
+                               bool force_bitonic = false) {
   constexpr uint32_t kCap = NT * ITEMS;
   static_assert(ITEMS >= 4, "the padded counters need cap/4 >= NT words of slack");
   const uint32_t tid = threadIdx.x;
-  if (m <= (uint32_t)kRankMax) {
+  if (m <= rank_max && m <= (uint32_t)NT) {
     count_algo(algo, kAlgoRank, m);
 #pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
@@ -117,6 +136,11 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     __syncthreads();
     if (tid < m) { s.k[rank] = key[0]; s.i[rank] = idx[0]; }
     __syncthreads();
+    return;
+  }
+  if (force_bitonic) {
+    count_algo(algo, kAlgoBitonic, m);
+    cta_bitonic_pairs<NT, ITEMS>(key, idx, m, s);
     return;
   }
   uint64_t mn = ~0ULL, mx = 0;
@@ -210,14 +234,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
   if (__syncthreads_or(crowd)) {
     // clustered keys: bitonic sort of the whole bucket
     count_algo(algo, kAlgoBitonic, m);
-    const uint32_t P = next_pow2_u32(m);
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-      const uint32_t e = r * NT + tid;
-      if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
-    }
-    for (uint32_t e = m + tid; e < P; e += NT) { s.k[e] = ~0ULL; s.i[e] = ~0u; }
-    block_bitonic_sort<NT>(s.k, s.i, (int)P);
+    cta_bitonic_pairs<NT, ITEMS>(key, idx, m, s);
     restore_common_key<NT>(s, m, s_by_pos, s_key_all);
     return;
   }

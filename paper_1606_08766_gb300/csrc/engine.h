@@ -65,9 +65,13 @@ struct rsort_ctx {
   // tunable "target_bucket": automatic fan-outs aim at final buckets of this
   // many keys (mostly inside the 1025..2048-key in-SM size class)
   uint32_t target_bucket = rsort::kTargetBucket;
-  // tunable "medium_sort": buckets of 1025..4096 keys are sorted by the
-  // equal-width bins (0, default) or by quicksort with tree-median pivots (1)
-  int medium_sort = 0;
+  // in-SM size classes and algorithms (tunables "small_cap", "mid_cap",
+  // "rank_max", "sort_small", "sort_mid", "sort_medium"; "medium_sort" sets
+  // the mid and medium classes to quicksort (1) or bins (0) at once)
+  rsort::LocalPlan local;
+  // tunable "target_bucket@c": fan-out target for segments of ceil(log2 m) = c
+  // (0: target_bucket)
+  uint32_t target_by_class[33] = {};
   // tunable "max_levels": partition levels before every bucket is final
   // (1..3, default 3); buckets still above one SM's capacity after the last
   // level are merge-sorted through global memory by one CTA each

@@ -179,6 +179,8 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   __shared__ uint64_t scan_sm[NT / 32];
   __shared__ uint32_t s_item;
   const FinalItem* list = items + (uint64_t)CLS * cap;
+  const uint32_t rank_max = st->local.rank_max;
+  const bool bitonic = st->local.algo[CLS - kClassSmall] == kLocalBitonic;
   uint64_t key[IT];
   uint32_t idx[IT];
   int64_t it = next_item(st, CLS, cap, &s_item);
@@ -189,7 +191,7 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
   }
   while (it >= 0) {
     cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
-                           red, scan_sm, st->algo_elems);
+                           red, scan_sm, st->algo_elems, rank_max, bitonic);
     // claim and start loading the next bucket before this one is stored, so
     // its loads are in flight while the stores go out
     const int64_t it2 = next_item(st, CLS, cap, &s_item);
@@ -322,7 +324,7 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   }
   {
     Scope sc(e, "local_sort_mid");
-    if (e.medium_sort == 1)
+    if (e.local.algo[kClassMid - kClassSmall] == kLocalQuick)
       k_local_quicksort<kLocalThreads, (int)kMidCap, kClassMid>
           <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kMidCap), e.stream>>>(
               st, items, item_cap, B, 0x243f6a8885a308d3ULL);
@@ -333,7 +335,7 @@ void launch_local_sort(const LaunchEnv& e, DevState* st, const FinalItem* items,
   }
   {
     Scope sc(e, "local_sort_medium");
-    if (e.medium_sort == 1)
+    if (e.local.algo[kClassMedium - kClassSmall] == kLocalQuick)
       k_local_quicksort<kLocalThreads, kBucketCap, kClassMedium>
           <<<e.num_sms * 2, kLocalThreads, qs_smem_bytes(kBucketCap), e.stream>>>(
               st, items, item_cap, B, 0x9e3779b97f4a7c15ULL);

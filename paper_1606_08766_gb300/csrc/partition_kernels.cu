@@ -42,8 +42,9 @@ struct Scope {
 // ---------------------------------------------------------------------------
 
 __global__ void k_init_plain(DevState* st, SegIn* list_l1, FinalItem* items, uint64_t n,
-                             uint32_t k1, int direct, uint64_t final_cap) {
+                             uint32_t k1, int direct, uint64_t final_cap, LocalPlan local) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->local = local;
   st->nseg[0] = st->nseg[1] = 0;
   for (int c = 0; c < kNumClasses; ++c) {
     st->nfinal_c[c] = 0;
@@ -109,7 +110,10 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       if (in.k_hint >= 1) {
         k = min(in.k_hint, kmax_level);
       } else {
-        const uint64_t want = ((uint64_t)in.m + P.target_bucket - 1) / P.target_bucket;
+        const uint32_t cls = ceil_log2_dev(in.m);
+        const uint32_t tb = (cls <= 32 && P.target_by_class[cls]) ? P.target_by_class[cls]
+                                                                  : P.target_bucket;
+        const uint64_t want = ((uint64_t)in.m + tb - 1) / tb;
         k = (uint32_t)umax64(2, umin64(want, kmax_level));
       }
       const uint64_t a = (in.k_hint >= 1 && P.level1_oversample)
@@ -1410,7 +1414,7 @@ void launch_plain_groups(const LaunchEnv& e, const uint64_t* offsets, uint32_t k
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,
                        uint64_t n, uint32_t k1, int direct, uint64_t final_cap) {
   Scope sc(e, "init");
-  k_init_plain<<<1, 32, 0, e.stream>>>(st, list0, items, n, k1, direct, final_cap);
+  k_init_plain<<<1, 32, 0, e.stream>>>(st, list0, items, n, k1, direct, final_cap, e.local);
 }
 
 void set_partition_kernel_attributes() {

@@ -106,6 +106,7 @@ struct Plan {
   int wd_max_k = 0;         // levels with at most this many buckets run warp-direct
   int wide_scatter_k = 1024;  // levels with at least this many buckets use wide sub-tiles
   uint32_t target_bucket = kTargetBucket;  // automatic fan-out target
+  uint32_t target_by_class[33] = {};       // per segment-size class (0: target_bucket)
   int unit_scatter = 1;     // stored bucket ids + whole-unit scatter where it fits
   uint64_t samp_extra = 0;  // sorted-sample slots past the sample (overpartitioning)
   uint64_t fine_cap = 0;    // fine partition counters (overpartitioning)
@@ -164,8 +165,12 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   const uint64_t segs_deep = n / (kBucketCap + 1) + 1;
   p.seg_cap = std::max<uint64_t>(g1, segs_deep);
   const uint32_t kmax1 = k1 >= 2 ? k1 : kMaxKDeep;
+  // automatic fan-outs aim at the smallest target any segment class uses
+  uint64_t tmin = p.target_bucket;
+  for (int c = 0; c <= 32; ++c)
+    if (p.target_by_class[c] && p.target_by_class[c] < tmin) tmin = p.target_by_class[c];
   // level 1
-  p.bucket_cap1 = k1 >= 2 ? (uint64_t)k1 * g1 : n / p.target_bucket + g1 + 1;
+  p.bucket_cap1 = k1 >= 2 ? (uint64_t)k1 * g1 : n / tmin + g1 + 1;
   p.bucket_cap1 = std::min<uint64_t>(p.bucket_cap1, (uint64_t)kmax1 * g1);
   const uint64_t a1 = k1 >= 2 ? 16ull * ceil_log2_host(k1) : (uint64_t)kDeepOversample;
   p.samp_cap1 = std::min<uint64_t>(n, a1 * p.bucket_cap1);
@@ -174,7 +179,7 @@ void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int
   p.hist_cap1 = ((uint64_t)kmax1 * (n / p.W1) + p.bucket_cap1) * kPartWarps;
   p.schunk_cap1 = p.samp_cap1 / kSampleChunk + g1 + 1;
   // deeper levels
-  const uint64_t bucket_capd = n / p.target_bucket + segs_deep + 1;
+  const uint64_t bucket_capd = n / tmin + segs_deep + 1;
   const uint64_t samp_capd = std::min<uint64_t>(n, (uint64_t)kDeepOversample * bucket_capd);
   const uint64_t chunk_capd = n / p.Wd + segs_deep + 1;
   const uint64_t hist_capd = ((uint64_t)kMaxKDeep * (n / p.Wd) + bucket_capd) * kPartWarps;
@@ -213,6 +218,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level
   P.warp_direct = kmax_level <= p.wd_max_k ? 1 : 0;
   P.wide_scatter_k = p.wide_scatter_k;
   P.target_bucket = p.target_bucket;
+  for (int i = 0; i <= 32; ++i) P.target_by_class[i] = p.target_by_class[i];
   P.unit_scatter = p.unit_scatter;
   return P;
 }
@@ -314,7 +320,40 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   }
   if (strcmp(name, "medium_sort") == 0) {
     if (v != 0 && v != 1) return RSORT_EINVAL;
-    c->medium_sort = (int)v;
+    c->local.algo[1] = c->local.algo[2] = v ? kLocalQuick : kLocalBins;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "sort_small") == 0) {
+    if (v != kLocalBins && v != kLocalBitonic) return RSORT_EINVAL;
+    c->local.algo[0] = (uint8_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "sort_mid") == 0 || strcmp(name, "sort_medium") == 0) {
+    if (v != kLocalBins && v != kLocalQuick && v != kLocalBitonic) return RSORT_EINVAL;
+    c->local.algo[strcmp(name, "sort_mid") == 0 ? 1 : 2] = (uint8_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "small_cap") == 0) {
+    if (v < 64 || v > (long long)kSmallCap) return RSORT_EINVAL;
+    c->local.small_cap = (uint32_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "mid_cap") == 0) {
+    if (v < 64 || v > (long long)kMidCap) return RSORT_EINVAL;
+    c->local.mid_cap = (uint32_t)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "rank_max") == 0) {
+    if (v < 0 || v > 128) return RSORT_EINVAL;
+    c->local.rank_max = (uint32_t)v;
+    return RSORT_OK;
+  }
+  if (strncmp(name, "target_bucket@", 14) == 0) {
+    char* end = nullptr;
+    const long cls = strtol(name + 14, &end, 10);
+    if (end == name + 14 || *end != '\0' || cls < 1 || cls > 32) return RSORT_EINVAL;
+    if (v != 0 && (v < 64 || v > kBucketCap)) return RSORT_EINVAL;
+    c->target_by_class[cls] = (uint32_t)v;
     return RSORT_OK;
   }
   if (strcmp(name, "unit_scatter") == 0) {
@@ -352,7 +391,9 @@ LaunchEnv env_of(rsort_ctx* c, cudaStream_t s) {
   e.num_sms = c->num_sms;
   e.timer = c->profiling ? &c->timer : nullptr;
   e.launches = &c->launches;
-  e.medium_sort = c->medium_sort;
+  e.local = c->local;
+  // a mid class below the small one is empty
+  if (e.local.mid_cap < e.local.small_cap) e.local.mid_cap = e.local.small_cap;
   return e;
 }
 
@@ -397,6 +438,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (n <= (uint64_t)kBucketCap) {
@@ -420,6 +462,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, c->max_levels);
@@ -627,6 +670,7 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   p.wd_max_k = c->wd_max_k;
   p.wide_scatter_k = c->wide_scatter_k;
   p.target_bucket = c->target_bucket;
+  for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
@@ -867,7 +911,38 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
     return RSORT_OK;
   }
   if (strcmp(name, "medium_sort") == 0) {
-    *value = c->medium_sort;
+    *value = (c->local.algo[1] == kLocalQuick && c->local.algo[2] == kLocalQuick) ? 1 : 0;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "sort_small") == 0) {
+    *value = c->local.algo[0];
+    return RSORT_OK;
+  }
+  if (strcmp(name, "sort_mid") == 0) {
+    *value = c->local.algo[1];
+    return RSORT_OK;
+  }
+  if (strcmp(name, "sort_medium") == 0) {
+    *value = c->local.algo[2];
+    return RSORT_OK;
+  }
+  if (strcmp(name, "small_cap") == 0) {
+    *value = c->local.small_cap;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "mid_cap") == 0) {
+    *value = c->local.mid_cap;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "rank_max") == 0) {
+    *value = c->local.rank_max;
+    return RSORT_OK;
+  }
+  if (strncmp(name, "target_bucket@", 14) == 0) {
+    char* end = nullptr;
+    const long cls = strtol(name + 14, &end, 10);
+    if (end == name + 14 || *end != '\0' || cls < 1 || cls > 32) return RSORT_EINVAL;
+    *value = c->target_by_class[cls];
     return RSORT_OK;
   }
   if (strcmp(name, "unit_scatter") == 0) {

@@ -62,8 +62,23 @@ enum : int {
   kAlgoInOrder = 5,  // all keys equal and already in position order
   kNumAlgos = 6
 };
-constexpr uint32_t kSmallCap = 1024;
-constexpr uint32_t kMidCap = 2048;
+constexpr uint32_t kSmallCap = 1024;   // capacity of the small-class kernel
+constexpr uint32_t kMidCap = 2048;     // capacity of the mid-class kernel
+// In-SM algorithm of a size class (LocalPlan::algo):
+enum : uint8_t { kLocalBins = 0, kLocalQuick = 1, kLocalBitonic = 2 };
+
+// The size-dependent choice of the in-SM sort, fixed per call (defaults from
+// hand sweeps; an autotuned table may replace them):
+//   buckets of at most small_cap keys go to the small-class kernel, at most
+//   mid_cap to the mid-class kernel, the rest (<= kBucketCap) to the medium
+//   one; rank_max bounds rank-by-counting; algo[class - 1] picks bins (with
+//   bitonic for clustered keys), quicksort (mid / medium only) or bitonic.
+struct LocalPlan {
+  uint32_t small_cap = 1024;  // <= kSmallCap
+  uint32_t mid_cap = 2048;    // small_cap..kMidCap
+  uint32_t rank_max = 64;     // <= 128 (the small kernel's threads)
+  uint8_t algo[3] = {kLocalBins, kLocalBins, kLocalBins};  // small, mid, medium
+};
 
 // A segment waiting to be partitioned (input of a level).
 struct SegIn {
@@ -108,6 +123,7 @@ struct DevState {
   uint32_t cursor_c[kNumClasses];  // work counters of the in-SM sort kernels
   uint64_t class_elems[kNumClasses];  // elements handed to each size class
   uint64_t algo_elems[kNumAlgos];     // elements finished by each in-SM algorithm
+  LocalPlan local;                    // the call's in-SM size classes and algorithms
   uint32_t error;           // capacity / wait errors (bit flags)
   uint32_t max_bucket_l1;   // largest level-1 bucket
   uint32_t levels_used;
@@ -143,6 +159,9 @@ struct LevelParams {
   int warp_direct;        // 1: per-warp sub-chunks scattered straight to HBM
   int wide_scatter_k;     // levels with at least this many buckets scatter 4096-key sub-tiles
   uint32_t target_bucket; // automatic fan-out aims at buckets of this many keys
+  // per segment-size class c = ceil(log2 m): the fan-out target for segments
+  // of that class (0: target_bucket)
+  uint32_t target_by_class[33] = {};
   int no_tie_break = 0;   // 1: classify by key only (the NTB ablation)
   int stable = 1;         // 1: buckets keep input order (the partition step's
                           // layout); 0: a full sort's deeper level, ranked by
@@ -275,8 +294,9 @@ __device__ __forceinline__ void push_final(DevState* st, FinalItem* items, uint6
                                            const FinalItem& f, uint32_t err_flag) {
   const int cls = f.kind == kKindCopy ? kClassCopy
                   : f.kind == kKindBig ? kClassBig
-                  : (f.size <= kSmallCap ? kClassSmall
-                                         : (f.size <= kMidCap ? kClassMid : kClassMedium));
+                  : (f.size <= st->local.small_cap
+                         ? kClassSmall
+                         : (f.size <= st->local.mid_cap ? kClassMid : kClassMedium));
   // one atomic per (warp, class): the lanes appending to the same list share it
   const uint32_t act = __activemask();
   const uint32_t peers = __match_any_sync(act, (uint32_t)cls);
@@ -327,7 +347,7 @@ struct LaunchEnv {
   int num_sms;
   KernelTimer* timer;   // may be null
   uint64_t* launches;   // launch counter
-  int medium_sort = 0;  // in-SM sort of buckets of 1025..4096 keys: 0 bins, 1 quicksort
+  LocalPlan local;      // in-SM size classes and algorithms (written to DevState at init)
 };
 
 void launch_init_plain(const LaunchEnv& e, DevState* st, SegIn* list0, FinalItem* items,

@@ -98,3 +98,18 @@ def test_torch_generator_matches_numpy(name, n, p):
         assert np.count_nonzero(a != b) <= max(1, n // 1000)
     else:
         np.testing.assert_array_equal(a, b)
+
+
+def test_torch_segmented_matches_numpy():
+    """The device generator of the batched instance draws the same segment
+    sizes and duplicate choices as the numpy one, and keys equal up to the
+    last bits of log / sqrt / cos."""
+    import torch  # noqa: F401
+    for ns, ml, cap in [(700, 16, None), (50, 20, 1 << 21), (1, 3, None)]:
+        a, oa = instances.segmented_f64(ns, ml, seed=3, total_cap=cap)
+        b, ob = instances.segmented_f64_torch(ns, ml, seed=3, total_cap=cap)
+        np.testing.assert_array_equal(oa.astype(np.int64), ob.numpy())
+        av, bv = a.view(np.float64), b.numpy()
+        assert np.abs(av - bv).max() <= 4e-15 * max(1.0, np.abs(av).max())
+        # exact duplicates sit at the same positions
+        np.testing.assert_array_equal(av[1:] == av[:-1], bv[1:] == bv[:-1])

@@ -250,3 +250,38 @@ def test_partition_balance_is_robust_to_duplicates(oracle_mod):
     assert uni < 1.5
     for name in ("zero", "deter_dupl", "rand_dupl"):
         assert imbalance(name) <= 1.1 * uni, name
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("n", range(0, 6))
+def test_parallel_sort_brute_force_ternary(oracle_mod, n, threads):
+    # the all-core timing oracle meets the same brute-force pin as the serial
+    # one, for thread counts below, at and above n
+    for vec in itertools.product(range(3), repeat=n):
+        keys = np.array(vec, dtype=np.uint64)
+        ko, po = oracle_mod.sort_parallel(keys, threads=threads)
+        expect = _brute_force_perm(vec)
+        np.testing.assert_array_equal(po, expect)
+        np.testing.assert_array_equal(ko, keys[expect])
+
+
+@pytest.mark.parametrize("threads", [2, 3, 7, 16])
+@pytest.mark.parametrize("n,universe", [(100_003, 2**64), (100_003, 5), (1, 2)])
+def test_parallel_sort_matches_numpy_stable_argsort(oracle_mod, n, universe, threads):
+    rng = np.random.default_rng(n + threads)
+    keys = rng.integers(0, universe, size=n, dtype=np.uint64) if universe < 2**64 \
+        else rng.integers(0, 2**64 - 1, size=n, dtype=np.uint64)
+    ko, po = oracle_mod.sort_parallel(keys, threads=threads)
+    expect = np.argsort(keys, kind="stable").astype(np.uint32)
+    np.testing.assert_array_equal(po, expect)
+    np.testing.assert_array_equal(ko, keys[expect])
+
+
+def test_parallel_sort_f64(oracle_mod):
+    order = _golden_f64()
+    rng = np.random.default_rng(11)
+    shuffled = np.tile(order, 50)[rng.permutation(order.shape[0] * 50)]
+    ko, po = oracle_mod.sort_parallel(shuffled, oracle_mod.KEY_F64, threads=6)
+    np.testing.assert_array_equal(ko, np.repeat(order, 50))
+    # ties keep position order
+    assert all(po[j] < po[j + 1] for j in range(po.shape[0] - 1) if ko[j] == ko[j + 1])
