@@ -355,6 +355,11 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                32 bytes of positions), holding each bucket's incomplete
  *                last unit in shared memory; 0: the staged scatter, which
  *                classifies again.
+ *   atomic_scatter  1: levels of rsort_sort / rsort_segmented after the
+ *                first (whose buckets may leave in any order) keep the ids of
+ *                their classify pass and scatter with a small-footprint
+ *                kernel that ranks by shared-memory atomics; 0 (default): the
+ *                staged scatter.
  *   wide_scatter_k  levels with at least this many buckets stage 4096-key
  *                sub-tiles with 512 threads when shared memory allows
  *                (default 1024).

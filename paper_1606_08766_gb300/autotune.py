@@ -6,6 +6,8 @@ number of levels and the splitter counts are tuned per size).  On one GPU the
 same choice is made per segment and per bucket, and this module measures it on
 the device instead of fixing it by hand:
 
+* the scatter of a sort's deeper levels: staged, or ranked by shared-memory
+  atomics in a small-footprint kernel (``atomic_scatter``);
 * the in-SM sort of a bucket, per bucket-size class: the rank-by-counting
   threshold (``rank_max``), bins or bitonic for the small class
   (``sort_small``), bins, quicksort or bitonic for the mid and medium classes
@@ -47,9 +49,11 @@ import torch
 
 from .binding import Context
 
-# Knobs of the in-SM sort: (name, candidates, default).  Tuned in this order,
-# each with the choices made before it in place.
+# Knobs timed on the mixed batches -- the scatter of the deeper levels, then
+# the in-SM sort: (name, candidates, default).  Tuned in this order, each with
+# the choices made before it in place.
 IN_SM_KNOBS = (
+    ("atomic_scatter", (0, 1), 0),
     ("rank_max", (0, 16, 32, 64, 128), 64),
     ("sort_small", (0, 2), 0),
     ("small_cap", (256, 512, 768, 1024), 1024),

@@ -85,6 +85,10 @@ struct rsort_ctx {
   // in whole 8-element units (1, default), or classify again in the staged
   // scatter (0)
   int unit_scatter = 1;
+  // tunable "atomic_scatter": unordered levels (a full sort's levels after the
+  // first) scatter with the small-footprint kernel ranked by shared-memory
+  // atomics (1) or the staged scatter (0, default)
+  int atomic_scatter = 0;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

@@ -1627,9 +1627,17 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   // its second classification, except in the warp-direct scatter and at
   // 1024+ buckets, where the staged scatter's L2-resident write frontiers
   // were the bottleneck and the extra id stream measured slower.
+  // With atomic_scatter, an unordered level (a full sort's levels after the
+  // first) keeps the ids of its classify pass and ranks by shared-memory
+  // atomics in the small-footprint scatter (measured slower than the staged
+  // scatter at 2^28 keys with ~171 buckets per segment; a tuner candidate).
   const bool units = P.unit_scatter && stable && !P.warp_direct && src.bid != nullptr &&
                      kmax_level > 32 && unit_scatter_fits((uint32_t)kmax_level);
-  if (!units && (P.warp_direct || kmax_level >= 1024)) src.bid = nullptr;
+  const bool atomics = P.atomic_scatter && !stable && !P.warp_direct && src.bid != nullptr &&
+                       atomic_scatter_fits((uint32_t)kmax_level);
+  if (!units && !atomics && (P.warp_direct || kmax_level >= 1024)) src.bid = nullptr;
+  // (the staged classify below stores the ids of an unordered level: at these
+  // fan-outs it measured faster than the register-streaming one)
   if (units) {
     launch_classify_ids(e, P, st, segs, src, ssamp_key, ssamp_idx, hist, (uint32_t)kmax_level,
                         mode, nm[4]);
@@ -1660,6 +1668,8 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   }
   if (units) {
     launch_scatter_units(e, P, st, segs, src, hist, dst, (uint32_t)kmax_level, unmap_out, nm[8]);
+  } else if (atomics) {
+    launch_scatter_atomic(e, P, st, segs, src, hist, dst, (uint32_t)kmax_level, unmap_out, nm[8]);
   } else {
     Scope sc(e, nm[8]);
     if (P.warp_direct)

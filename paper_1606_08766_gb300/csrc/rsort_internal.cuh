@@ -172,6 +172,8 @@ struct LevelParams {
   int unit_scatter = 1;   // 1: a stable level with at most kUnitMaxK buckets
                           // stores bucket ids when classifying and scatters
                           // whole 8-element units (unit_scatter.cu)
+  int atomic_scatter = 0; // 1: an unordered level scatters with the
+                          // small-footprint atomic-ranked kernel
 };
 
 // AMS-sort overpartitioning of a one-segment partition step: b*k fine
@@ -376,6 +378,10 @@ bool unit_scatter_fits(uint32_t kmax);
 void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
                          const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t* ssi,
                          uint32_t* hist, uint32_t kmax, int mode, const char* name);
+bool atomic_scatter_fits(uint32_t kmax);
+void launch_scatter_atomic(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                           const LevelSeg* segs, Src src, const uint32_t* hist_scan, Dst dst,
+                           uint32_t kmax, int unmap_out, const char* name);
 void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st,
                           const LevelSeg* segs, Src src, const uint32_t* hist_scan, Dst dst,
                           uint32_t kmax, int unmap_out, const char* name);

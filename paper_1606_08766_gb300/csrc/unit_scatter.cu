@@ -538,6 +538,118 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Scatter of an unordered level (a full sort's levels after the first): the
+// in-SM sort orders (key, position) pairs, so elements of a bucket may leave
+// in any order.  Every element takes its rank from one shared-memory atomic
+// on its bucket's counter -- no per-warp tables, no carries (a bucket's run
+// per sub-tile is long at these fan-outs) -- so the kernel is small enough
+// for several CTAs per SM to hide each other's latency.
+// ---------------------------------------------------------------------------
+constexpr int kSaThreads = 256;
+constexpr int kSaItems = 8;
+constexpr int kSaTile = kSaThreads * kSaItems;  // 2048 elements per sub-tile
+
+__host__ __device__ inline size_t sa_smem_bytes(uint32_t kmax) {
+  return (size_t)kSaTile * (8 + 4 + 2) + (size_t)kmax * 12;
+}
+
+template <int NT, bool HAS_IDX>
+__global__ void __launch_bounds__(NT, 4)
+k_scatter_atomic(const DevState* st, const LevelSeg* segs, Src src, const uint32_t* hist_scan,
+                 Dst dst, uint32_t kmax, int conv) {
+  constexpr int IT = kSaItems;
+  constexpr int ST = NT * IT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* p = smem_raw;
+  uint64_t* skey = (uint64_t*)p; p += (size_t)ST * 8;
+  uint32_t* sidx = (uint32_t*)p; p += (size_t)ST * 4;
+  uint32_t* cnt = (uint32_t*)p; p += (size_t)kmax * 4;    // counts, then rank bases
+  uint32_t* opos = (uint32_t*)p; p += (size_t)kmax * 4;   // running output position
+  uint32_t* dlt = (uint32_t*)p; p += (size_t)kmax * 4;    // output position - sorted slot
+  uint16_t* sb = (uint16_t*)p;                            // bucket of every sorted slot
+  __shared__ uint64_t scan_sm[NT / 32];
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t pol_keep = l2_evict_last_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const uint32_t tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const uint32_t q0 = (uint32_t)warp * (IT * 32) + lane;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    const uint32_t k = sg.k;
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
+    const uint32_t per = (k + NT - 1) / NT;
+    const uint32_t bb0 = min(tid * per, k), bb1 = min(bb0 + per, k);
+    __syncthreads();  // the previous chunk is done with every shared array
+    for (uint32_t b = tid; b < k; b += NT) {
+      opos[b] = (uint32_t)(hist_scan[sg.hist_off + (uint64_t)b * sg.nunits + cl] + sg.delta);
+      cnt[b] = 0;
+    }
+    for (uint64_t b0 = cs; b0 < ce; b0 += ST) {
+      const uint32_t len = (uint32_t)umin64(ST, ce - b0);
+      uint64_t key[IT];
+      uint32_t idx[IT], bid[IT], rank[IT];
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        const uint32_t q = q0 + r * 32;
+        bid[r] = 0xffffffffu;
+        if (q < len) {
+          key[r] = ld_stream_u64(src.key + b0 + q, pol);
+          idx[r] = HAS_IDX ? ld_stream_u32(src.idx + b0 + q, pol)
+                           : (uint32_t)(b0 + q - sg.start);
+          bid[r] = ld_stream_u16(src.bid + b0 + q, pol);
+        }
+      }
+      __syncthreads();  // (A) counters cleared, previous sub-tile written out
+#pragma unroll
+      for (int r = 0; r < IT; ++r)
+        if (bid[r] != 0xffffffffu) rank[r] = atomicAdd(&cnt[bid[r]], 1u);
+      __syncthreads();  // (B) counts complete
+      {
+        uint32_t loc = 0;
+        for (uint32_t b = bb0; b < bb1; ++b) loc += cnt[b];
+        uint64_t tot;
+        uint32_t run = (uint32_t)block_excl_scan_u64<NT>(loc, &tot, scan_sm);
+        for (uint32_t b = bb0; b < bb1; ++b) {
+          const uint32_t t = cnt[b];
+          cnt[b] = run;                    // rank base of the bucket in the sub-tile
+          dlt[b] = opos[b] - run;          // modulo 2^32: positions are below 2^32
+          opos[b] += t;
+          run += t;
+        }
+      }
+      __syncthreads();  // (C) bases in place
+#pragma unroll
+      for (int r = 0; r < IT; ++r) {
+        const uint32_t b = bid[r];
+        if (b != 0xffffffffu) {
+          const uint32_t q = cnt[b] + rank[r];
+          skey[q] = conv_key(key[r], conv);
+          sidx[q] = idx[r];
+          sb[q] = (uint16_t)b;
+        }
+      }
+      __syncthreads();  // (D) sub-tile sorted by bucket
+      // runs of ~m/k elements per bucket: the sectors at their ends are
+      // completed by the next sub-tile, so the stores ask the L2 to keep
+      // them until then
+      for (uint32_t q = tid; q < len; q += NT) {
+        const uint32_t d = dlt[sb[q]] + q;
+        st_keep_u64(dst.key + d, skey[q], pol_keep);
+        st_keep_u32(dst.idx + d, sidx[q], pol_keep);
+      }
+      // counters back to zero for the next sub-tile (bases are no longer read)
+      __syncthreads();
+      for (uint32_t b = bb0; b < bb1; ++b) cnt[b] = 0;
+    }
+  }
+}
+
 // Dynamic shared memory limit of the unit scatter (0 until set or if refused).
 size_t g_us_smem_max = 0;
 
@@ -576,6 +688,10 @@ void set_unit_scatter_attributes() {
       limit = 0;
   }
   g_us_smem_max = limit;
+  cudaFuncSetAttribute(k_scatter_atomic<kSaThreads, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa_smem_bytes(kMaxK));
+  cudaFuncSetAttribute(k_scatter_atomic<kSaThreads, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa_smem_bytes(kMaxK));
   cudaGetLastError();
 }
 
@@ -592,6 +708,33 @@ void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
   Scope sc(e, name);
   k_classify_ids<256><<<(int)(grid ? grid : 1), 256, smem, e.stream>>>(st, segs, src, ssk, ssi,
                                                                        hist, kmax, mode, vec);
+}
+
+void launch_scatter_atomic(const LaunchEnv& e, const LevelParams& P, DevState* st,
+                           const LevelSeg* segs, Src src, const uint32_t* hist_scan, Dst dst,
+                           uint32_t kmax, int unmap_out, const char* name) {
+  const int conv = (src.map_f64 && !unmap_out) ? 1 : ((!src.map_f64 && unmap_out) ? 2 : 0);
+  const size_t smem = sa_smem_bytes(kmax);
+  int nb = 0;
+  if (src.idx)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter_atomic<kSaThreads, true>,
+                                                  kSaThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scatter_atomic<kSaThreads, false>,
+                                                  kSaThreads, smem);
+  if (nb < 1) nb = 1;
+  const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms * nb);
+  Scope sc(e, name);
+  if (src.idx)
+    k_scatter_atomic<kSaThreads, true><<<(int)(grid ? grid : 1), kSaThreads, smem, e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv);
+  else
+    k_scatter_atomic<kSaThreads, false><<<(int)(grid ? grid : 1), kSaThreads, smem, e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv);
+}
+
+bool atomic_scatter_fits(uint32_t kmax) {
+  return kmax <= (uint32_t)kMaxK && sa_smem_bytes(kmax) <= sa_smem_bytes(kMaxK);
 }
 
 void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st,
