@@ -52,7 +52,9 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    "L2.scatter": 25.29,   # 0.9671 + 0.7303 GB at 2^26 keys
+    "L1.scatter": 23.45,   # 0.7608 + 0.8124 GB at 2^26 keys (k_scatter_units)
+    "L1.classify": 9.23,   # 0.5392 + 0.0807 GB (k_classify_ids, ids included)
+    "L2.scatter": 25.29,   # 0.9671 + 0.7303 GB
     "L2.classify": 9.39,   # 0.5519 + 0.0783 GB
 }
 
