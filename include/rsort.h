@@ -360,6 +360,10 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                their classify pass and scatter with a small-footprint
  *                kernel that ranks by shared-memory atomics; 0 (default): the
  *                staged scatter.
+ *   bulk_classify  1: the classify pass that stores bucket ids stages its
+ *                keys through bulk copies (cp.async.bulk on shared-memory
+ *                barriers) into a 4-stage ring when the key array is 16-byte
+ *                aligned; 0 (default): 16-byte loads into registers.
  *   wide_scatter_k  levels with at least this many buckets stage 4096-key
  *                sub-tiles with 512 threads when shared memory allows
  *                (default 1024).

@@ -89,6 +89,10 @@ struct rsort_ctx {
   // first) scatter with the small-footprint kernel ranked by shared-memory
   // atomics (1) or the staged scatter (0, default)
   int atomic_scatter = 0;
+  // tunable "bulk_classify": the id-storing classify stages its keys through
+  // bulk copies into a shared-memory ring (1) or loads them into registers
+  // (0, default: measured faster, 0.97 vs 1.12 ms at 2^28 keys)
+  int bulk_classify = 0;
   rsort::KernelTimer timer;
   rsort::TimerImpl timer_impl;
   std::mutex mu;

@@ -109,6 +109,7 @@ struct Plan {
   uint32_t target_by_class[33] = {};       // per segment-size class (0: target_bucket)
   int unit_scatter = 1;     // stored bucket ids + whole-unit scatter where it fits
   int atomic_scatter = 0;   // unordered levels: atomic-ranked small-footprint scatter
+  int bulk_classify = 0;    // id-storing classify staged by bulk copies
   uint64_t samp_extra = 0;  // sorted-sample slots past the sample (overpartitioning)
   uint64_t fine_cap = 0;    // fine partition counters (overpartitioning)
   // arena offsets
@@ -222,6 +223,7 @@ LevelParams level_params(const Plan& p, int level, uint64_t seed, int kmax_level
   for (int i = 0; i <= 32; ++i) P.target_by_class[i] = p.target_by_class[i];
   P.unit_scatter = p.unit_scatter;
   P.atomic_scatter = p.atomic_scatter;
+  P.bulk_classify = p.bulk_classify;
   return P;
 }
 
@@ -368,6 +370,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->atomic_scatter = (int)v;
     return RSORT_OK;
   }
+  if (strcmp(name, "bulk_classify") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->bulk_classify = (int)v;
+    return RSORT_OK;
+  }
   if (c->server) return RSORT_EINVAL;  // serving tunables are fixed once it runs
   if (strcmp(name, "serve_slots") == 0) {
     if (v < 1 || v > 8) return RSORT_EINVAL;
@@ -448,6 +455,7 @@ Plan plan_sort(rsort_ctx* c, uint64_t n, uint32_t p_virtual) {
   for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   p.atomic_scatter = c->atomic_scatter;
+  p.bulk_classify = c->bulk_classify;
   const uint32_t k1 = p_virtual >= 2 ? p_virtual : 0;
   if (n <= (uint64_t)kBucketCap) {
     p.n = n;
@@ -473,6 +481,7 @@ Plan plan_segmented(rsort_ctx* c, uint64_t n, uint32_t num_segments) {
   for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   p.atomic_scatter = c->atomic_scatter;
+  p.bulk_classify = c->bulk_classify;
   const uint64_t g1 = std::min<uint64_t>(num_segments, n / (kBucketCap + 1) + 1);
   plan_levels(p, n, 0, std::max<uint64_t>(g1, 2), c->num_sms, c->max_levels);
   p.final_cap += num_segments;
@@ -682,6 +691,7 @@ rsort_status partition_impl(rsort_ctx* c, rsort_key_type type, const void* d_key
   for (int i = 0; i <= 32; ++i) p.target_by_class[i] = c->target_by_class[i];
   p.unit_scatter = c->unit_scatter;
   p.atomic_scatter = c->atomic_scatter;
+  p.bulk_classify = c->bulk_classify;
   const uint32_t kk = k < 2 ? 2 : k;  // capacities as for two buckets when k = 1
   plan_levels(p, n, kk, 1, c->num_sms, 1);
   p.final_cap = 4;
@@ -961,6 +971,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "atomic_scatter") == 0) {
     *value = c->atomic_scatter;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "bulk_classify") == 0) {
+    *value = c->bulk_classify;
     return RSORT_OK;
   }
   if (strcmp(name, "serve_batch_keys") == 0) {

@@ -146,6 +146,7 @@ enum : uint32_t {
   kErrSchunkCap = 1u << 5,
   kErrBucketCap = 1u << 6,
   kErrBadOffsets = 1u << 7,
+  kErrWait = 1u << 8,         // a bounded wait on a bulk copy gave up
 };
 
 // Parameters of one level, fixed on the host.
@@ -174,6 +175,8 @@ struct LevelParams {
                           // whole 8-element units (unit_scatter.cu)
   int atomic_scatter = 0; // 1: an unordered level scatters with the
                           // small-footprint atomic-ranked kernel
+  int bulk_classify = 0;  // 1: the id-storing classify stages its keys by
+                          // bulk copies (16-byte aligned key arrays)
 };
 
 // AMS-sort overpartitioning of a one-segment partition step: b*k fine

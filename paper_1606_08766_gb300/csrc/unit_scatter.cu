@@ -29,6 +29,7 @@
 // The carry area holds 7 (key, position) slots per bucket, so the scatter
 // serves levels with at most kUnitMaxK buckets.
 #include "async_copy.cuh"
+#include "bulk_copy.cuh"
 #include "rsort_internal.cuh"
 #include "splitters.cuh"
 
@@ -195,6 +196,199 @@ k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < sg.k; b += NT)
       hist[sg.hist_off + (uint64_t)b * sg.nunits + cl] = cnt[b];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same classify pass with its keys staged by bulk copies: one thread
+// keeps a ring of kCbStages shared-memory stages of kCbStageKeys keys filled
+// through the tensor memory accelerator (cp.async.bulk, completed on one
+// mbarrier per stage), running ahead across the CTA's chunks, so every SM
+// has up to 2 x 4 x 16 KB of loads in flight without holding registers for
+// them.  A stage starts at an even position (16-byte aligned when the key
+// array is) and ends at an even one; a chunk's odd last key is read directly.
+// ---------------------------------------------------------------------------
+constexpr int kCbStageKeys = 2048;
+constexpr int kCbStages = 4;
+
+__host__ __device__ inline size_t classify_bulk_smem_bytes(size_t common) {
+  return ((common + 127) & ~(size_t)127) + (size_t)kCbStages * kCbStageKeys * 8 +
+         (size_t)kCbStages * 16;
+}
+
+// Warp-specialised: NC consumer threads classify, one producer warp (the
+// last) streams the stages.  Per stage a "full" barrier (one arrival with the
+// expected bytes) and an "empty" barrier (one arrival per consumer warp);
+// there is no block barrier inside a chunk.  Every wait is bounded: a wait
+// that gives up raises kErrWait, the CTA drains its copies and returns.
+template <int NC>
+__global__ void __launch_bounds__(NC + 32, 2)
+k_classify_bulk(DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
+                const uint32_t* ssi, uint32_t* hist, uint32_t kmax, int mode, size_t common) {
+  constexpr int NT = NC + 32;
+  constexpr int NCW = NC / 32;         // consumer warps
+  constexpr int SK = kCbStageKeys;
+  constexpr int NST = kCbStages;
+  constexpr int PER = SK / (2 * NC);   // key pairs per consumer thread per stage
+  constexpr int R = 2 * PER;
+  static_assert(PER * 2 * NC == SK, "a stage is whole pairs per consumer thread");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Splitters sp;
+  uint32_t* cnt;
+  {
+    unsigned char* p = smem_raw;
+    const size_t Kp = next_pow2_u32(kmax);
+    sp.mode = mode & 1;
+    sp.ntb = (mode >> 1) & 1;
+    sp.tree = nullptr;
+    sp.tbl = nullptr;
+    if (sp.mode == 0) {
+      sp.tree = (uint64_t*)p;
+      p += Kp * 8;
+    } else {
+      sp.tbl = (uint32_t*)p;
+      p += (size_t)4 << table_bits_for((uint32_t)Kp);
+    }
+    sp.key = (uint64_t*)p; p += (size_t)kmax * 8;
+    sp.idx = (uint32_t*)p; p += (size_t)kmax * 4;
+    cnt = (uint32_t*)p; p += (size_t)kmax * 4;
+    sp.rend = (uint16_t*)p;
+  }
+  uint64_t* stage = (uint64_t*)(smem_raw + ((common + 127) & ~(size_t)127));
+  uint64_t* full = stage + (size_t)NST * SK;
+  uint64_t* empty = full + NST;
+  __shared__ uint32_t s_abort;
+  const uint64_t pol = l2_evict_first_policy();
+  const uint64_t total = st->total_chunks;
+  const uint32_t G = st->cur_nseg;
+  const uint32_t tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const bool producer = warp == NCW;
+  if (tid == 0) {
+    for (int b = 0; b < NST; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], NCW);
+    }
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  uint32_t next = 0;   // stages issued (producer) / consumed (consumers) so far
+  uint32_t cur_g = 0xffffffffu;
+  for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
+    const LevelSeg sg = segs[g];
+    if (__syncthreads_or(s_abort != 0)) break;
+    if (g != cur_g) {
+      load_splitters<NT>(sg, ssk, ssi, sp);
+      cur_g = g;
+    }
+    for (uint32_t b = tid; b < sg.k; b += NT) cnt[b] = 0;
+    __syncthreads();
+    const uint64_t cl = c - sg.chunk_off;
+    const uint64_t cs = sg.start + cl * sg.W;
+    const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
+    const uint64_t ps = cs & ~1ull, pe = ce & ~1ull;
+    const uint32_t nstg = pe > ps ? (uint32_t)((pe - ps + SK - 1) / SK) : 0u;
+    if (producer) {
+      if (lane == 0) {
+        for (uint32_t s = 0; s < nstg; ++s, ++next) {
+          const uint32_t buf = next % NST, use = next / NST;
+          if (use > 0 && !mbar_wait_bounded(&empty[buf], (use - 1) & 1u, kBulkWaitPolls)) {
+            atomicOr(&s_abort, 1u);
+            break;
+          }
+          const uint64_t a = ps + (uint64_t)s * SK;
+          const uint64_t b = umin64(a + SK, pe);
+          fence_proxy_async_smem();
+          bulk_copy_g2s(stage + (size_t)buf * SK, src.key + a, (uint32_t)((b - a) * 8),
+                        &full[buf], pol);
+        }
+      }
+      next = __shfl_sync(0xffffffffu, next, 0);
+    } else {
+      auto count = [&](bool v, uint32_t b) {
+        const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
+        if (__all_sync(0xffffffffu, v && b == bl)) {
+          if (lane == 0) atomicAdd(&cnt[bl], 32u);
+        } else if (v) {
+          atomicAdd(&cnt[b], 1u);
+        }
+      };
+      for (uint32_t s = 0; s < nstg; ++s, ++next) {
+        const uint32_t buf = next % NST, use = next / NST;
+        const bool ok = mbar_wait_bounded(&full[buf], use & 1u, kBulkWaitPolls);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) atomicOr(&s_abort, 1u);
+          break;
+        }
+        const uint64_t a = ps + (uint64_t)s * SK;
+        const uint64_t b = umin64(a + SK, pe);
+        const uint64_t* stg = stage + (size_t)buf * SK;
+        uint64_t key[R];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+          const uint32_t j = r * NC + tid;
+          key[2 * r] = key[2 * r + 1] = 0;
+          if (a + 2 * j < b) {
+            const uint4 v = *reinterpret_cast<const uint4*>(stg + 2 * j);
+            key[2 * r] = ((uint64_t)v.y << 32) | v.x;
+            key[2 * r + 1] = ((uint64_t)v.w << 32) | v.z;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[buf]);  // this warp is done with the stage
+#pragma unroll
+        for (int e = 0; e < R; ++e) key[e] = src.map_f64 ? f64_to_ordered(key[e]) : key[e];
+        uint32_t bk[R];
+        classify_batch<R>(key, bk, [&](int e) {
+          const uint64_t pos = a + 2 * ((uint64_t)(e >> 1) * NC + tid) + (e & 1);
+          if (pos < cs || pos >= ce) return 0u;
+          return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
+        }, sp);
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+          const uint64_t pos = a + 2 * ((uint64_t)r * NC + tid);
+          const bool v0 = pos < b && pos >= cs;
+          const bool v1 = pos + 1 < b;
+          if (v0 && v1) {
+            *reinterpret_cast<uint32_t*>(src.bid + pos) = bk[2 * r] | (bk[2 * r + 1] << 16);
+          } else if (v1) {
+            src.bid[pos + 1] = (uint16_t)bk[2 * r + 1];
+          }
+          count(v0, bk[2 * r]);
+          count(v1, bk[2 * r + 1]);
+        }
+      }
+      // the consumer warps agree on the stage count (an abort ends them early)
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // an odd chunk end: its last key is read directly
+    if ((ce & 1) && ce - 1 >= cs && tid == 0) {
+      uint64_t x[1] = {load_key(src, ce - 1)};
+      uint32_t bk[1];
+      classify_batch<1>(x, bk, [&](int) {
+        return src.idx ? src.idx[ce - 1] : (uint32_t)(ce - 1 - sg.start);
+      }, sp);
+      src.bid[ce - 1] = (uint16_t)bk[0];
+      atomicAdd(&cnt[bk[0]], 1u);
+    }
+    __syncthreads();
+    for (uint32_t b = tid; b < sg.k; b += NT)
+      hist[sg.hist_off + (uint64_t)b * sg.nunits + cl] = cnt[b];
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) atomicOr(&st->error, kErrWait);
+    // copies still in flight must land before the CTA's shared memory goes:
+    // the producer waits for the phases of the last stages it issued (a
+    // landed one answers at once)
+    if (producer && lane == 0) {
+      const uint32_t from = next > (uint32_t)NST ? next - NST : 0u;
+      for (uint32_t i = from; i < next; ++i)
+        mbar_wait_bounded(&full[i % NST], (i / NST) & 1u, kBulkWaitPolls);
+    }
   }
 }
 
@@ -670,6 +864,9 @@ void set_unit_scatter_attributes() {
   cudaFuncSetAttribute(k_classify_ids<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)umax64(classify_ids_smem_bytes(kMaxK, 0),
                                    classify_ids_smem_bytes(kMaxK, 1)));
+  cudaFuncSetAttribute(k_classify_bulk<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)classify_bulk_smem_bytes(umax64(classify_ids_smem_bytes(kMaxK, 0),
+                                                            classify_ids_smem_bytes(kMaxK, 1))));
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -698,6 +895,19 @@ void set_unit_scatter_attributes() {
 void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
                          const LevelSeg* segs, Src src, const uint64_t* ssk, const uint32_t* ssi,
                          uint32_t* hist, uint32_t kmax, int mode, const char* name) {
+  if (P.bulk_classify && ((uintptr_t)src.key & 15) == 0) {
+    // keys staged by bulk copies (needs a 16-byte aligned key array)
+    const size_t common = classify_ids_smem_bytes(kmax, mode);
+    const size_t smem = classify_bulk_smem_bytes(common);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_bulk<256>, 256 + 32, smem);
+    if (nb < 1) nb = 1;
+    const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms * nb);
+    Scope sc(e, name);
+    k_classify_bulk<256><<<(int)(grid ? grid : 1), 256 + 32, smem, e.stream>>>(
+        st, segs, src, ssk, ssi, hist, kmax, mode, common);
+    return;
+  }
   const size_t smem = classify_ids_smem_bytes(kmax, mode);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_ids<256>, 256, smem);

@@ -277,6 +277,7 @@ CONFIGS = {
     "deep_levels_stable": {"deep_levels_stable": 1},
     "staged_scatter": {"unit_scatter": 0},
     "atomic_scatter": {"atomic_scatter": 1},
+    "bulk_classify": {"bulk_classify": 1},
     "bitonic_everywhere": {"sort_small": 2, "sort_mid": 2, "sort_medium": 2, "rank_max": 0},
     "shifted_classes": {"small_cap": 256, "mid_cap": 1024, "rank_max": 128, "sort_mid": 1,
                         "target_bucket@17": 768, "target_bucket@18": 2560,
