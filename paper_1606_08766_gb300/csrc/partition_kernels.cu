@@ -1028,11 +1028,11 @@ k_scatter_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* 
 }
 
 // Collect the buckets of the level: bucket sizes follow from the scanned
-// histogram.  Buckets that fit one SM, equality buckets of a stable level
-// (both bounding splitters share one key, so every element has that key and
-// the stable scatter already left them in position order) and empty ones are
-// final; the rest become segments of the next level.  After an unstable
-// scatter an equality bucket is a bucket like any other, and its elements
+// histogram.  Buckets that fit one SM, equality buckets of a stable level on
+// input in position order (both bounding splitters share one key, so every
+// element has that key and the stable scatter left them in position order)
+// and empty ones are final; the rest become segments of the next level.
+// Otherwise an equality bucket is a bucket like any other, and its elements
 // arrive at the in-SM sort in no particular order.
 __global__ void __launch_bounds__(256)
 k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_t* hist_scan,
@@ -1056,8 +1056,11 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
     }
     if (P.level == 1) atomicMax(&st->max_bucket_l1, size);
     if (!emit_final || size == 0) continue;
+    // buckets keep position order only if the level is stable and its input
+    // was in position order
+    const bool ordered = P.stable && P.in_order;
     bool eq = false;
-    if (P.stable && b >= 1 && b + 1 < sg.k) {
+    if (ordered && b >= 1 && b + 1 < sg.k) {
       const uint64_t klo = ssk[sg.samp_off + ((uint64_t)b * sg.S) / sg.k];
       const uint64_t khi = ssk[sg.samp_off + ((uint64_t)(b + 1) * sg.S) / sg.k];
       eq = klo == khi;
@@ -1070,7 +1073,7 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
       it.where = where;
       it.kind = (eq || size == 1)      ? kKindCopy
                 : size > kBucketCap    ? kKindBig
-                : P.stable             ? kKindSort
+                : ordered              ? kKindSort
                                        : kKindSortAny;
       if (it.kind == kKindBig) atomicAdd((unsigned long long*)&st->big_items, 1ull);
       push_final(st, items, P.final_cap, it, kErrFinalCap);
@@ -1631,10 +1634,13 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   // first) keeps the ids of its classify pass and ranks by shared-memory
   // atomics in the small-footprint scatter (measured slower than the staged
   // scatter at 2^28 keys with ~171 buckets per segment; a tuner candidate).
-  const bool units = P.unit_scatter && stable && !P.warp_direct && src.bid != nullptr &&
-                     kmax_level > 32 && unit_scatter_fits((uint32_t)kmax_level);
-  const bool atomics = P.atomic_scatter && !stable && !P.warp_direct && src.bid != nullptr &&
-                       atomic_scatter_fits((uint32_t)kmax_level);
+  // (a full sort's level 1 may scatter without keeping input order: the unit
+  // scatter then ranks by shared-memory atomics)
+  const bool units = P.unit_scatter && (stable || P.level == 1) && !P.warp_direct &&
+                     src.bid != nullptr && kmax_level > 32 &&
+                     unit_scatter_fits((uint32_t)kmax_level);
+  const bool atomics = !units && P.atomic_scatter && !stable && !P.warp_direct &&
+                       src.bid != nullptr && atomic_scatter_fits((uint32_t)kmax_level);
   if (!units && !atomics && (P.warp_direct || kmax_level >= 1024)) src.bid = nullptr;
   // (the staged classify below stores the ids of an unordered level: at these
   // fan-outs it measured faster than the register-streaming one)

@@ -269,8 +269,10 @@ void enqueue_levels_and_local(rsort_ctx* c, Workspace& ws, const Plan& p, const 
     LevelParams P = level_params(p, L, seed, kmax);
     // level 1 keeps input order inside buckets; deeper levels may not (the
     // in-SM sort orders (key, position) pairs either way)
-    P.stable = L == 1 ? 1 : c->deep_levels_stable;
-    P.in_order = L == 1 ? 1 : (L == 2 ? 1 : c->deep_levels_stable);
+    // a level's input is in position order only after stable levels
+    P.stable = L == 1 ? c->level1_stable : c->deep_levels_stable;
+    P.in_order = L == 1 ? 1
+                 : (L == 2 ? c->level1_stable : (c->level1_stable && c->deep_levels_stable));
     Src src;
     if (L == 1) {
       src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
@@ -315,6 +317,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
   if (strcmp(name, "deep_levels_stable") == 0) {
     if (v != 0 && v != 1) return RSORT_EINVAL;
     c->deep_levels_stable = (int)v;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "level1_stable") == 0) {
+    if (v != 0 && v != 1) return RSORT_EINVAL;
+    c->level1_stable = (int)v;
     return RSORT_OK;
   }
   if (strcmp(name, "max_levels") == 0) {
@@ -924,6 +931,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "deep_levels_stable") == 0) {
     *value = c->deep_levels_stable;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "level1_stable") == 0) {
+    *value = c->level1_stable;
     return RSORT_OK;
   }
   if (strcmp(name, "max_levels") == 0) {

@@ -441,7 +441,11 @@ __device__ __forceinline__ uint32_t block_excl_max_u32(uint32_t v, uint32_t* sm)
 
 // HAS_IDX: the level reads stored positions (deeper levels); otherwise the
 // position is implicit (level 1: offset in the segment).
-template <int NT, bool HAS_IDX>
+// STABLE: elements of a bucket keep input order (ranks from per-warp counters
+// and a prefix over the warps); otherwise (a full sort's level 1, whose
+// buckets the in-SM sort orders by (key, position) anyway) every element takes
+// its rank from one shared-memory atomic on its bucket's counter.
+template <int NT, bool HAS_IDX, bool STABLE>
 __global__ void __launch_bounds__(NT, 1)
 k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_t* hist_scan,
                 Dst dst, uint32_t kmax, int conv, uint32_t aoff) {
@@ -480,7 +484,10 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
   const uint32_t ltmask = lanemask_lt();
   uint16_t* my_cnt = wcnt + (size_t)warp * kst;
   uint8_t* my_win = wwin + (size_t)warp * kmax;
+  uint32_t* ucnt = reinterpret_cast<uint32_t*>(wcnt);  // unordered: one counter per bucket
   for (uint32_t u = tid; u < umax; u += NT) unit_b[u] = 0;
+  if (!STABLE)
+    for (uint32_t b = tid; b < kmax; b += NT) ucnt[b] = 0;
 
   for (uint64_t c = blockIdx.x; c < total; c += gridDim.x) {
     const uint32_t g = find_seg(segs, G, c, [](const LevelSeg& x) { return x.chunk_off; });
@@ -528,10 +535,16 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
     for (uint64_t s = 0; s < nst; ++s) {
       load(s + 1, nkey, nidx, nbid);
       // -- 1. rank every element among its bucket's elements of this warp
-      //    (stable: earlier rounds, then lower lanes)
+      //    (stable: earlier rounds, then lower lanes), or of the sub-tile
+      //    (unordered: a shared-memory atomic)
+      uint32_t lrank[IT];
+      if constexpr (!STABLE) {
+#pragma unroll
+        for (int r = 0; r < IT; ++r)
+          if (bid[r] != 0xffffffffu) lrank[r] = atomicAdd(&ucnt[bid[r]], 1u);
+      } else {
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
-      uint32_t lrank[IT];
 #pragma unroll
       for (int r = 0; r < IT; ++r) {
         const uint32_t b = bid[r];
@@ -567,6 +580,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         __syncwarp();
         lrank[r] = c0 + __popc(peers & ltmask);
       }
+      }  // STABLE
       __syncthreads();  // (A) every warp's counts are in
       // -- 2. per bucket: exclusive prefix over the warps' counts (in place),
       //    the bucket's elements t in this sub-tile, its virtual run
@@ -574,7 +588,16 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       //    of (u, t) places every bucket's elements in the sorted sub-tile and
       //    its units in the unit list
       uint32_t loc_t = 0, loc_u = 0;
-      {
+      if constexpr (!STABLE) {
+        for (uint32_t b = bb0; b < bb1; ++b) {
+          const uint32_t t = ucnt[b];
+          ucnt[b] = 0;  // ready for the next sub-tile (its atomics follow barriers)
+          const uint32_t u = (((meta[b] >> 24) & 7u) + t) / kUnit;
+          sbase[b] = t | (u << 16);
+          loc_t += t;
+          loc_u += u;
+        }
+      } else {
         uint32_t b = bb0;
         for (; (per & 1) == 0 && b + 1 < bb1; b += 2) {
           uint32_t tot2 = 0;
@@ -646,7 +669,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       for (int r = 0; r < IT; ++r) {
         const uint32_t b = bid[r];
         if (b != 0xffffffffu) {
-          const uint32_t q = sbase[b] + my_cnt[b] + lrank[r];
+          const uint32_t q = sbase[b] + (STABLE ? (uint32_t)my_cnt[b] : 0u) + lrank[r];
           skey[q] = conv_key(key[r], conv);
           sidx[q] = HAS_IDX ? idx[r] : pos0 + r * 32;
         }
@@ -872,14 +895,20 @@ void set_unit_scatter_attributes() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa{};
   size_t limit = 0;
-  if (cudaFuncGetAttributes(&fa, k_scatter_units<kUsThreads, true>) == cudaSuccess &&
+  if (cudaFuncGetAttributes(&fa, k_scatter_units<kUsThreads, true, true>) == cudaSuccess &&
       (size_t)optin > fa.sharedSizeBytes) {
     limit = (size_t)optin - fa.sharedSizeBytes;
     if (limit > us_smem_bytes(kUnitMaxK)) limit = us_smem_bytes(kUnitMaxK);
-    if (cudaFuncSetAttribute(k_scatter_units<kUsThreads, true>,
+    if (cudaFuncSetAttribute(k_scatter_units<kUsThreads, true, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess ||
-        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false>,
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess)
       limit = 0;
@@ -955,13 +984,19 @@ void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st
   const uint32_t aoff = (uint32_t)(((64 - ((uintptr_t)dst.key & 63)) & 63) / 8);
   const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms);
   Scope sc(e, name);
-  if (src.idx)
-    k_scatter_units<kUsThreads, true><<<(int)(grid ? grid : 1), kUsThreads, us_smem_bytes(kmax),
-                                        e.stream>>>(st, segs, src, hist_scan, dst, kmax, conv,
-                                                    aoff);
+  const int g = (int)(grid ? grid : 1);
+  const size_t smem = us_smem_bytes(kmax);
+  if (src.idx && P.stable)
+    k_scatter_units<kUsThreads, true, true><<<g, kUsThreads, smem, e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv, aoff);
+  else if (P.stable)
+    k_scatter_units<kUsThreads, false, true><<<g, kUsThreads, smem, e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv, aoff);
+  else if (src.idx)
+    k_scatter_units<kUsThreads, true, false><<<g, kUsThreads, smem, e.stream>>>(
+        st, segs, src, hist_scan, dst, kmax, conv, aoff);
   else
-    k_scatter_units<kUsThreads, false><<<(int)(grid ? grid : 1), kUsThreads,
-                                         us_smem_bytes(kmax), e.stream>>>(
+    k_scatter_units<kUsThreads, false, false><<<g, kUsThreads, smem, e.stream>>>(
         st, segs, src, hist_scan, dst, kmax, conv, aoff);
 }
 

@@ -274,7 +274,8 @@ CONFIGS = {
     "tree_warpdirect": {"classifier": 0, "warp_direct_max_k": 2048},
     "table_warpdirect": {"classifier": 1, "warp_direct_max_k": 2048},
     "wide_scatter_everywhere": {"classifier": 1, "wide_scatter_k": 2},
-    "deep_levels_stable": {"deep_levels_stable": 1},
+    "deep_levels_stable": {"deep_levels_stable": 1, "level1_stable": 1},
+    "level1_stable": {"level1_stable": 1},
     "staged_scatter": {"unit_scatter": 0},
     "atomic_scatter": {"atomic_scatter": 1},
     "bulk_classify": {"bulk_classify": 1},
