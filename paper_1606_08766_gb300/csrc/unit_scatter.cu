@@ -395,26 +395,34 @@ k_classify_bulk(DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk
 // ---------------------------------------------------------------------------
 // Scatter in whole units
 // ---------------------------------------------------------------------------
+// The stable scatter keeps per-warp counters and winner slots (512 threads,
+// 4096-element sub-tiles); the unordered one needs one counter per bucket,
+// and the room that frees holds longer sub-tiles (more elements per thread).
 constexpr int kUsThreads = 512;
-constexpr int kUsItems = 8;
-constexpr int kUsTile = kUsThreads * kUsItems;  // 4096 elements per sub-tile
+constexpr int kUsItems = 8;            // stable
+constexpr int kUsItemsAny = 12;        // unordered (6144-element sub-tiles)
+// bits of the per-bucket meta word
+constexpr int kMetaUnitShift = 14;     // sorted slot + 8 below (14 bits)
+constexpr int kMetaCarryShift = 25;    // first unit (11 bits) below
+constexpr int kMetaPhShift = 28;       // carry count (3 bits) below, phantoms (3 bits)
 
-__host__ __device__ inline uint32_t us_max_units(uint32_t kmax) {
-  return (kUsTile + kCarry * kmax) / kUnit + 1;
+__host__ __device__ inline uint32_t us_max_units(uint32_t kmax, uint32_t st) {
+  return (st + kCarry * kmax) / kUnit + 1;
 }
 
-__host__ __device__ inline size_t us_smem_bytes(uint32_t kmax) {
-  constexpr int NW = kUsThreads / 32;
+__host__ __device__ inline size_t us_smem_bytes(uint32_t kmax, uint32_t nt, uint32_t it,
+                                                bool stable) {
+  const uint32_t nw = nt / 32, st = nt * it;
   size_t b = 0;
-  b += (size_t)kUsTile * 8;                      // sorted keys
+  b += (size_t)st * 8;                           // sorted keys
   b += (size_t)kmax * kCarry * 8;                // carried keys
-  b += (size_t)kUsTile * 4;                      // sorted positions
+  b += (size_t)st * 4;                           // sorted positions
   b += (size_t)kmax * kCarry * 4;                // carried positions
   b += (size_t)kmax * 8;                         // per-bucket obase + meta
   b += (size_t)(kmax + 1) * 4;                   // sbase
-  b += (size_t)NW * cnt_stride(kmax) * 2;        // per-warp counters
-  b += (size_t)us_max_units(kmax) * 2 + 2;       // unit -> bucket
-  b += (size_t)NW * kmax;                        // per-warp winner slots
+  b += stable ? (size_t)nw * cnt_stride(kmax) * 2 : (size_t)kmax * 4;  // counters
+  b += (size_t)us_max_units(kmax, st) * 2 + 2;   // unit -> bucket
+  b += stable ? (size_t)nw * kmax : 0;           // per-warp winner slots
   return (b + 15) & ~(size_t)15;
 }
 
@@ -445,14 +453,15 @@ __device__ __forceinline__ uint32_t block_excl_max_u32(uint32_t v, uint32_t* sm)
 // and a prefix over the warps); otherwise (a full sort's level 1, whose
 // buckets the in-SM sort orders by (key, position) anyway) every element takes
 // its rank from one shared-memory atomic on its bucket's counter.
-template <int NT, bool HAS_IDX, bool STABLE>
+template <int NT, int IT, bool HAS_IDX, bool STABLE>
 __global__ void __launch_bounds__(NT, 1)
 k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_t* hist_scan,
                 Dst dst, uint32_t kmax, int conv, uint32_t aoff) {
   constexpr int NW = NT / 32;
-  constexpr int IT = kUsItems;
   constexpr int ST = NT * IT;
-  static_assert(ST == kUsTile, "sub-tile size");
+  static_assert(ST + kUnit < (1 << kMetaUnitShift), "sorted slots fit the meta word");
+  static_assert(((ST + kCarry * kUnitMaxK) / kUnit) < (1 << (kMetaCarryShift - kMetaUnitShift)),
+                "unit indices fit the meta word");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* p = smem_raw;
   uint64_t* skey = (uint64_t*)p; p += (size_t)ST * 8;
@@ -462,15 +471,16 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
   // per-bucket state (two flat word arrays, so that both the bucket-ordered
   // and the interleaved phases touch consecutive words):
   //   obase  output position of the bucket's current unit start (mod 2^32)
-  //   meta   sorted slot of that unit's first slot + 8 (13 bits; the unit
+  //   meta   sorted slot of that unit's first slot + 8 (14 bits; the unit
   //          may begin with up to 7 carried slots) | first unit in the unit
-  //          list << 13 (11 bits) | carry count << 24 | phantoms << 27
+  //          list << 14 (11 bits) | carry count << 25 | phantoms << 28
   uint32_t* obase = (uint32_t*)p; p += (size_t)kmax * 4;
   uint32_t* meta = (uint32_t*)p; p += (size_t)kmax * 4;
   uint32_t* sbase = (uint32_t*)p; p += (size_t)(kmax + 1) * 4;
   const uint32_t kst = cnt_stride(kmax);
-  uint16_t* wcnt = (uint16_t*)p; p += (size_t)NW * kst * 2;
-  const uint32_t umax = us_max_units(kmax);
+  uint16_t* wcnt = (uint16_t*)p;
+  p += STABLE ? (size_t)NW * kst * 2 : (size_t)kmax * 4;
+  const uint32_t umax = us_max_units(kmax, ST);
   uint16_t* unit_b = (uint16_t*)p; p += (size_t)umax * 2 + 2;
   uint8_t* wwin = (uint8_t*)p;
   __shared__ uint64_t scan_sm[NW];
@@ -511,11 +521,11 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
                                      sg.delta);
       const uint32_t a = (p0 - aoff) & (kUnit - 1);
       obase[b] = p0 - a;
-      meta[b] = (a << 24) | (a << 27);
+      meta[b] = (a << kMetaCarryShift) | (a << kMetaPhShift);
     }
     const uint32_t q0 = (uint32_t)warp * (IT * 32) + lane;
-    uint64_t key[IT], nkey[IT];
-    uint32_t idx[IT], nidx[IT], bid[IT], nbid[IT];
+    uint64_t key[IT];
+    uint32_t idx[IT], bid[IT];
     auto load = [&](uint64_t s, uint64_t (&kk)[IT], uint32_t (&ii)[IT], uint32_t (&bb)[IT]) {
       const uint64_t b0 = cs + s * ST;
 #pragma unroll
@@ -533,7 +543,6 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
     };
     load(0, key, idx, bid);
     for (uint64_t s = 0; s < nst; ++s) {
-      load(s + 1, nkey, nidx, nbid);
       // -- 1. rank every element among its bucket's elements of this warp
       //    (stable: earlier rounds, then lower lanes), or of the sub-tile
       //    (unordered: a shared-memory atomic)
@@ -592,7 +601,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t t = ucnt[b];
           ucnt[b] = 0;  // ready for the next sub-tile (its atomics follow barriers)
-          const uint32_t u = (((meta[b] >> 24) & 7u) + t) / kUnit;
+          const uint32_t u = (((meta[b] >> kMetaCarryShift) & 7u) + t) / kUnit;
           sbase[b] = t | (u << 16);
           loc_t += t;
           loc_u += u;
@@ -611,7 +620,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const uint32_t t = h ? (tot2 >> 16) : (tot2 & 0xffffu);
-            const uint32_t u = (((meta[b + h] >> 24) & 7u) + t) / kUnit;
+            const uint32_t u = (((meta[b + h] >> kMetaCarryShift) & 7u) + t) / kUnit;
             sbase[b + h] = t | (u << 16);
             loc_t += t;
             loc_u += u;
@@ -625,7 +634,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
             wcnt[(size_t)w * kst + b] = (uint16_t)t;
             t += cnt;
           }
-          const uint32_t u = (((meta[b] >> 24) & 7u) + t) / kUnit;
+          const uint32_t u = (((meta[b] >> kMetaCarryShift) & 7u) + t) / kUnit;
           sbase[b] = t | (u << 16);
           loc_t += t;
           loc_u += u;
@@ -639,9 +648,10 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t tu = sbase[b], t = tu & 0xffffu, u = tu >> 16;
           const uint32_t m = meta[b];
-          const uint32_t cb = (m >> 24) & 7u;
+          const uint32_t cb = (m >> kMetaCarryShift) & 7u;
           sbase[b] = run_t;
-          meta[b] = (m & 0xff000000u) | (run_u << 13) | (run_t + kUnit - cb);
+          meta[b] = (m & (0x3fu << kMetaCarryShift)) | (run_u << kMetaUnitShift) |
+                    (run_t + kUnit - cb);
           if (u) unit_b[run_u] = (uint16_t)(b + 1);
           run_t += t;
           run_u += u;
@@ -675,6 +685,9 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         }
       }
       __syncthreads();  // (C) the sorted sub-tile and the unit buckets are in
+      // the next sub-tile's loads go out now, into the same registers, and
+      // land while this one is written
+      load(s + 1, key, idx, bid);
       // -- 4. whole units out: 8 consecutive lanes store one unit (slots
       //    before the carry count come from the carry area, phantoms are
       //    skipped)
@@ -682,9 +695,10 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         const uint32_t u = e / kUnit, j = e % kUnit;
         const uint32_t b = (uint32_t)unit_b[u] - 1;
         const uint32_t m = meta[b], ob = obase[b];
-        const uint32_t cb = (m >> 24) & 7u, ph = m >> 27;
-        const uint32_t v = kUnit * (u - ((m >> 13) & 0x7ffu)) + j;  // slot in the bucket's run
-        const uint32_t q = (m & 0x1fffu) - kUnit + v;                // sorted slot (if not carried)
+        const uint32_t cb = (m >> kMetaCarryShift) & 7u, ph = (m >> kMetaPhShift) & 7u;
+        // slot in the bucket's run, and its sorted slot (if not carried)
+        const uint32_t v = kUnit * (u - ((m >> kMetaUnitShift) & 0x7ffu)) + j;
+        const uint32_t q = (m & ((1u << kMetaUnitShift) - 1)) - kUnit + v;
         uint64_t kv;
         uint32_t iv;
         if (v < cb) {
@@ -706,8 +720,8 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       //    touch neighbouring carry rows; copies unrolled and predicated)
       for (uint32_t b = tid; b < k; b += NT) {
         const uint32_t m = meta[b];
-        const uint32_t cb = (m >> 24) & 7u;
-        const uint32_t qb = (m & 0x1fffu) - kUnit;  // sorted slot of run slot 0
+        const uint32_t cb = (m >> kMetaCarryShift) & 7u;
+        const uint32_t qb = (m & ((1u << kMetaUnitShift) - 1)) - kUnit;  // sorted slot of run slot 0
         const uint32_t L = cb + (sbase[b + 1] - sbase[b]), u = L / kUnit, nc = L % kUnit;
         // run slots [first, L) become carry slots [first - shift, L - shift)
         const uint32_t first = u == 0 ? cb : kUnit * u;
@@ -730,23 +744,17 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
           for (int j = 0; j < kCarry; ++j)
             if (first + j < L) cidx[b * kCarry + first + j - shift] = ci[j];
         }
-        const uint32_t ph = u == 0 ? (m >> 27) : 0u;
+        const uint32_t ph = u == 0 ? ((m >> kMetaPhShift) & 7u) : 0u;
         obase[b] += shift;
-        meta[b] = (nc << 24) | (ph << 27);
+        meta[b] = (nc << kMetaCarryShift) | (ph << kMetaPhShift);
       }
       for (uint32_t u = tid; u < U; u += NT) unit_b[u] = 0;
-#pragma unroll
-      for (int r = 0; r < IT; ++r) {
-        key[r] = nkey[r];
-        if (HAS_IDX) idx[r] = nidx[r];
-        bid[r] = nbid[r];
-      }
     }
     // the chunk's last, incomplete unit of every bucket (the rest of its
     // sectors belongs to the next chunk's range)
     for (uint32_t b = tid; b < k; b += NT) {
       const uint32_t m = meta[b], ob = obase[b];
-      const uint32_t cb = (m >> 24) & 7u, ph = m >> 27;
+      const uint32_t cb = (m >> kMetaCarryShift) & 7u, ph = (m >> kMetaPhShift) & 7u;
       for (uint32_t j = ph; j < cb; ++j) {
         dst.key[ob + j] = ckey[b * kCarry + j];
         dst.idx[ob + j] = cidx[b * kCarry + j];
@@ -880,7 +888,9 @@ size_t classify_ids_smem_bytes(uint32_t kmax, int mode) {
 }
 
 bool unit_scatter_fits(uint32_t kmax) {
-  return kmax <= (uint32_t)kUnitMaxK && us_smem_bytes(kmax) <= g_us_smem_max;
+  return kmax <= (uint32_t)kUnitMaxK &&
+         us_smem_bytes(kmax, kUsThreads, kUsItems, true) <= g_us_smem_max &&
+         us_smem_bytes(kmax, kUsThreads, kUsItemsAny, false) <= g_us_smem_max;
 }
 
 void set_unit_scatter_attributes() {
@@ -895,20 +905,22 @@ void set_unit_scatter_attributes() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa{};
   size_t limit = 0;
-  if (cudaFuncGetAttributes(&fa, k_scatter_units<kUsThreads, true, true>) == cudaSuccess &&
+  if (cudaFuncGetAttributes(&fa, k_scatter_units<kUsThreads, kUsItems, true, true>) == cudaSuccess &&
       (size_t)optin > fa.sharedSizeBytes) {
     limit = (size_t)optin - fa.sharedSizeBytes;
-    if (limit > us_smem_bytes(kUnitMaxK)) limit = us_smem_bytes(kUnitMaxK);
-    if (cudaFuncSetAttribute(k_scatter_units<kUsThreads, true, true>,
+    const size_t need = umax64(us_smem_bytes(kUnitMaxK, kUsThreads, kUsItems, true),
+                               us_smem_bytes(kUnitMaxK, kUsThreads, kUsItemsAny, false));
+    if (limit > need) limit = need;
+    if (cudaFuncSetAttribute(k_scatter_units<kUsThreads, kUsItems, true, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess ||
-        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false, true>,
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, kUsItems, false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess ||
-        cudaFuncSetAttribute(k_scatter_units<kUsThreads, true, false>,
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, kUsItemsAny, true, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess ||
-        cudaFuncSetAttribute(k_scatter_units<kUsThreads, false, false>,
+        cudaFuncSetAttribute(k_scatter_units<kUsThreads, kUsItemsAny, false, false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess)
       limit = 0;
@@ -985,18 +997,19 @@ void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st
   const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms);
   Scope sc(e, name);
   const int g = (int)(grid ? grid : 1);
-  const size_t smem = us_smem_bytes(kmax);
+  const size_t smem_s = us_smem_bytes(kmax, kUsThreads, kUsItems, true);
+  const size_t smem_a = us_smem_bytes(kmax, kUsThreads, kUsItemsAny, false);
   if (src.idx && P.stable)
-    k_scatter_units<kUsThreads, true, true><<<g, kUsThreads, smem, e.stream>>>(
+    k_scatter_units<kUsThreads, kUsItems, true, true><<<g, kUsThreads, smem_s, e.stream>>>(
         st, segs, src, hist_scan, dst, kmax, conv, aoff);
   else if (P.stable)
-    k_scatter_units<kUsThreads, false, true><<<g, kUsThreads, smem, e.stream>>>(
+    k_scatter_units<kUsThreads, kUsItems, false, true><<<g, kUsThreads, smem_s, e.stream>>>(
         st, segs, src, hist_scan, dst, kmax, conv, aoff);
   else if (src.idx)
-    k_scatter_units<kUsThreads, true, false><<<g, kUsThreads, smem, e.stream>>>(
+    k_scatter_units<kUsThreads, kUsItemsAny, true, false><<<g, kUsThreads, smem_a, e.stream>>>(
         st, segs, src, hist_scan, dst, kmax, conv, aoff);
   else
-    k_scatter_units<kUsThreads, false, false><<<g, kUsThreads, smem, e.stream>>>(
+    k_scatter_units<kUsThreads, kUsItemsAny, false, false><<<g, kUsThreads, smem_a, e.stream>>>(
         st, segs, src, hist_scan, dst, kmax, conv, aoff);
 }
 
