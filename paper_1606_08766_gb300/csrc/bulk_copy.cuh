@@ -75,6 +75,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Asks the L2 to fetch the 16-byte granules that lie wholly inside the bytes
+// [lo, hi) of global memory (an asynchronous hint: nothing waits for it, and
+// no byte outside the range is touched).
+__device__ __forceinline__ void prefetch_l2_range(const void* lo, const void* hi) {
+  const uintptr_t a = ((uintptr_t)lo + 15) & ~(uintptr_t)15;
+  const uintptr_t b = (uintptr_t)hi & ~(uintptr_t)15;
+  if (b > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(b - a))
+                 : "memory");
+}
+
 // Polls before a bulk copy's bytes are given up on (each try_wait may suspend
 // the thread for a system-dependent time before it reports "not yet"); a
 // copy of 16 KB lands within microseconds, so only a fault reaches the limit.
