@@ -419,6 +419,10 @@ constexpr int kUsItemsAny = 12;
 // placement, find their bytes on the way (measured at 2^28 keys: distance 1
 // 2.23 -> 2.08 ms, 2 -> 2.12, 3 -> 2.18)
 constexpr int kUsPrefetch = 1;
+// a bucket with at most this many whole units in a sub-tile writes their
+// records itself; more (skewed inputs) send the sub-tile through the unit
+// marks and a block max-scan instead
+constexpr int kUsDirectUnits = 16;
 // bits of the per-bucket meta word
 constexpr int kMetaUnitShift = 14;     // sorted slot + 8 below (14 bits)
 constexpr int kMetaCarryShift = 25;    // first unit (11 bits) below
@@ -514,6 +518,8 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
   uint8_t* wwin = (uint8_t*)p;
   __shared__ uint64_t scan_sm[NW];
   __shared__ uint32_t max_sm[NW];
+  __shared__ uint32_t s_big;  // some bucket has more than kUsDirectUnits units
+  if (threadIdx.x == 0) s_big = 0;
 
   const uint64_t pol = l2_evict_first_policy();
   const uint64_t total = st->total_chunks;
@@ -634,7 +640,8 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       //    the bucket's elements t in this sub-tile, its virtual run
       //    (carry + t) and the whole units u of that run; then one block scan
       //    of (u, t) places every bucket's elements in the sorted sub-tile and
-      //    its units in the unit list
+      //    its units in the unit list, and a bucket with few units writes
+      //    their records
       uint32_t loc_t = 0, loc_u = 0;
       if constexpr (!STABLE) {
         for (uint32_t b = bb0; b < bb1; ++b) {
@@ -684,6 +691,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
           block_excl_scan_u64<NT>(((uint64_t)loc_u << 32) | loc_t, &tot, scan_sm);
       {
         uint32_t run_t = (uint32_t)ex, run_u = (uint32_t)(ex >> 32);
+        bool big = false;
         for (uint32_t b = bb0; b < bb1; ++b) {
           const uint32_t tu = sbase[b], t = tu & 0xffffu, u = tu >> 16;
           const uint32_t m = meta[b];
@@ -691,19 +699,36 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
           sbase[b] = run_t;
           meta[b] = (m & (0x3fu << kMetaCarryShift)) | (run_u << kMetaUnitShift) |
                     (run_t + kUnit - cb);
-          if (u) unit_b[run_u] = (uint16_t)(b + 1);
+          if (u > (uint32_t)kUsDirectUnits) {
+            big = true;
+          } else if (u) {
+            const uint32_t ob = obase[b];
+            const uint32_t qv = run_t + kUnit - cb;
+            urec[run_u] = make_uint2(ob, qv | (((m >> kMetaCarryShift) & 0x3fu) << kRecFirstShift) |
+                                             (b << kRecBucketShift));
+            for (uint32_t d = 1; d < u; ++d)
+              urec[run_u + d] = make_uint2(ob + kUnit * d, (qv + kUnit * d) | (b << kRecBucketShift));
+          }
           run_t += t;
           run_u += u;
         }
+        if (big) s_big = 1u;
       }
       const uint32_t U = (uint32_t)(tot >> 32);
       if (tid == 0) sbase[k] = (uint32_t)tot;
       __syncthreads();  // (B) bucket bases and unit marks are in
-      // -- 3. the bucket of every unit (marks carry bucket + 1 at a bucket's
-      //    first unit; an inclusive max-scan fills the rest) and its record
-      //    (the marks are cleared for the next sub-tile), and the sub-tile
+      // -- 3. if a bucket had too many units to write their records: the
+      //    bucket of every unit (marks carry bucket + 1 at a bucket's first
+      //    unit; an inclusive max-scan fills the rest) and every unit's record
+      //    (the marks are cleared for the next sub-tile); then the sub-tile
       //    counting-sorted by bucket into shared memory
-      {
+      if (s_big) {
+        for (uint32_t b = bb0; b < bb1; ++b) {
+          const uint32_t m = meta[b];
+          const uint32_t uu = (((m >> kMetaCarryShift) & 7u) + sbase[b + 1] - sbase[b]) / kUnit;
+          if (uu) unit_b[(m >> kMetaUnitShift) & 0x7ffu] = (uint16_t)(b + 1);
+        }
+        __syncthreads();
         const uint32_t upt = (U + NT - 1) / NT;
         const uint32_t u0 = min(tid * upt, U), u1 = min(u0 + upt, U);
         uint32_t m = 0;
@@ -731,6 +756,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         }
       }
       __syncthreads();  // (C) the sorted sub-tile and the unit buckets are in
+      if (tid == 0) s_big = 0;
       // the next sub-tile's loads go out now, into the same registers, and
       // land while this one is written
       load(s + 1, key, idx, bid);
