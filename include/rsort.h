@@ -315,12 +315,19 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                rsort_submit); fixed once the runtime has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
  *                (64..4096, default 1536).
+ *   level1_stable  level 1 of rsort_sort / rsort_segmented: 1 keeps input
+ *                order inside buckets; 0 ranks elements by shared-memory
+ *                atomics (faster on distinct keys); 2 (default) decides on
+ *                the device per call: input order when at least 1/16 of the
+ *                level's buckets are equality buckets (both bounding
+ *                splitters hold one key, as with many copies of a key), whose
+ *                elements, kept in position order, are final at once.
+ *                rsort_partition always keeps input order.
  *   deep_levels_stable  1: the partition levels of rsort_sort /
  *                rsort_segmented after the first keep input order inside
  *                buckets; 0 (default): they rank elements by shared-memory
- *                atomics.  The result is the same (the in-SM sort orders
- *                (key, position) pairs); level 1 and rsort_partition always
- *                keep input order.
+ *                atomics.  The result is the same either way (the in-SM sort
+ *                orders (key, position) pairs).
  *   max_levels   partition levels of rsort_sort / rsort_segmented before
  *                every bucket is final (1..3, default 3).  A bucket still
  *                above 4096 keys after the last level is merge-sorted
@@ -330,9 +337,9 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *   size-dependent choice, applied per bucket; paper_1606_08766_gb300.autotune
  *   measures these on the device and writes a table of them):
  *   small_cap, mid_cap  buckets of at most small_cap keys (64..1024, default
- *                1024) are sorted by 128-thread CTAs, of at most mid_cap
- *                (64..2048, default 2048) by 256-thread CTAs, larger ones (up
- *                to 4096) by 512-thread CTAs.
+ *                1024) are sorted by 128-thread CTAs of 8 slots a thread, of
+ *                at most mid_cap (64..2048, default 2048) by 128-thread CTAs
+ *                of 16 slots, larger ones (up to 4096) by 512-thread CTAs.
  *   rank_max     buckets of at most this many keys (0..128, default 64) are
  *                sorted by rank-by-counting (Appendix "Fast Work-Inefficient
  *                Ranking").
@@ -348,18 +355,17 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                ceil(log2 m) = c keys (64..4096; 0 falls back to
  *                target_bucket): the bucket count of such a segment is
  *                ceil(m / target).
- *   unit_scatter  1 (default): a level that keeps input order inside buckets
- *                (level 1, the partition step) and has at most 1024 buckets
- *                stores every element's bucket id when it classifies, and
- *                its scatter writes whole 8-element units (64 bytes of keys,
- *                32 bytes of positions), holding each bucket's incomplete
- *                last unit in shared memory; 0: the staged scatter, which
- *                classifies again.
- *   atomic_scatter  1: levels of rsort_sort / rsort_segmented after the
- *                first (whose buckets may leave in any order) keep the ids of
- *                their classify pass and scatter with a small-footprint
- *                kernel that ranks by shared-memory atomics; 0 (default): the
- *                staged scatter.
+ *   unit_scatter  1 (default): a level with 33..1024 buckets stores every
+ *                element's bucket id when it classifies, and its scatter
+ *                writes whole 8-element units (64 bytes of keys, 32 bytes of
+ *                positions), holding each bucket's incomplete last unit in
+ *                shared memory; 0: the staged scatter, which classifies
+ *                again.
+ *   atomic_scatter  1: levels of rsort_sort / rsort_segmented that may
+ *                leave buckets in any order and do not take the unit scatter
+ *                keep the ids of their classify pass and scatter with a
+ *                small-footprint kernel that ranks by shared-memory atomics;
+ *                0 (default): the staged scatter.
  *   bulk_classify  1: the classify pass that stores bucket ids stages its
  *                keys through bulk copies (cp.async.bulk on shared-memory
  *                barriers) into a 4-stage ring when the key array is 16-byte

@@ -12,8 +12,8 @@ the device instead of fixing it by hand:
   threshold (``rank_max``), bins or bitonic for the small class
   (``sort_small``), bins, quicksort or bitonic for the mid and medium classes
   (``sort_mid``, ``sort_medium``), and the class cut-offs that pick the CTA
-  shape (``small_cap``: 128-thread CTAs up to it, ``mid_cap``: 256-thread CTAs
-  up to it, 512-thread CTAs above);
+  shape (``small_cap``: 128 threads of 8 slots up to it, ``mid_cap``: 128
+  threads of 16 slots up to it, 512-thread CTAs above);
 * the sample-sort fan-out of a segment, per segment-size class
   c = ceil(log2 m): the bucket size it aims at (``target_bucket@c``, i.e. the
   bucket count k = ceil(m / target)).

@@ -81,9 +81,10 @@ struct rsort_ctx {
   // default); level 1, the partition step, always keeps it
   int deep_levels_stable = 0;
   // tunable "level1_stable": level 1 of rsort_sort / rsort_segmented keeps
-  // input order inside buckets (1) or ranks by shared-memory atomics (0,
-  // default); rsort_partition always keeps it
-  int level1_stable = 0;
+  // input order inside buckets (1), ranks by shared-memory atomics (0), or
+  // keeps it only when at least 1/16 of its buckets are equality buckets,
+  // decided on the device (2, default); rsort_partition always keeps it
+  int level1_stable = 2;
   // tunable "unit_scatter": stable levels with at most rsort::kUnitMaxK
   // buckets store every element's bucket id in the classify pass and scatter
   // in whole 8-element units (1, default), or classify again in the staged

@@ -95,6 +95,11 @@ k_level_plan(DevState* st, const SegIn* list_in, LevelSeg* segs, LevelParams P, 
       G = 0;
     }
     if (G) st->levels_used = P.level;
+    if (P.level == 1) {
+      st->l1_eq = 0;
+      st->l1_nb = 0;
+      st->l1_ordered = 0;
+    }
     sG = G;
     for (int i = 0; i < 6; ++i) carry[i] = 0;
   }
@@ -246,8 +251,10 @@ k_sample_sort_chunks(const DevState* st, const LevelSeg* segs, uint64_t* samp_ke
         idx[r] = samp_idx[base + e];
       }
     }
-    cta_sort_pairs<NT, IT>(key, idx, len, [&] { return in_order != 0; }, s, red, scan_sm,
-                           nullptr);
+    cta_sort_pairs<NT, IT>(key, idx, len,
+                           [&] { return in_order == kOrderAuto ? st->l1_ordered != 0
+                                                               : in_order != 0; },
+                           s, red, scan_sm, nullptr);
     uint64_t* ok = sg.nschunks == 1 ? ssamp_key : samp_key;
     uint32_t* oi = sg.nschunks == 1 ? ssamp_idx : samp_idx;
     for (uint32_t t = threadIdx.x; t < len; t += NT) {
@@ -1027,6 +1034,33 @@ k_scatter_wd(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* 
   }
 }
 
+// Level 1 with its order left to the device (LevelParams::stable ==
+// kOrderAuto): counts the level's equality buckets, those whose two bounding
+// splitters hold one key (every element of such a bucket has that key, so in
+// position order it is final and skips the levels below).  The scatter and
+// the collect keep input order when they are at least 1/kAutoOrderShare of
+// the buckets (duplicate-heavy inputs) and rank by atomics otherwise.
+__global__ void __launch_bounds__(256)
+k_l1_order(DevState* st, const LevelSeg* segs, const uint64_t* ssk) {
+  const uint64_t total = st->total_buckets;
+  const uint32_t G = st->cur_nseg;
+  uint32_t cnt = 0;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = find_seg(segs, G, f, [](const LevelSeg& x) { return x.bkt_off; });
+    const LevelSeg& sg = segs[g];
+    const uint32_t b = (uint32_t)(f - sg.bkt_off);
+    if (b >= 1 && b + 1 < sg.k)
+      cnt += ssk[sg.samp_off + ((uint64_t)b * sg.S) / sg.k] ==
+                     ssk[sg.samp_off + ((uint64_t)(b + 1) * sg.S) / sg.k]
+                 ? 1u : 0u;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->l1_eq, cnt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->l1_nb = (uint32_t)umin64(total, 0xffffffffull);
+}
+
 // Collect the buckets of the level: bucket sizes follow from the scanned
 // histogram.  Buckets that fit one SM, equality buckets of a stable level on
 // input in position order (both bounding splitters share one key, so every
@@ -1040,6 +1074,12 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
           int last_level, int emit_final, uint64_t* offsets_out) {
   const uint64_t total = st->total_buckets;
   const uint32_t G = st->cur_nseg;
+  // buckets keep position order only if the level is stable and its input
+  // was in position order (level 1 records this for the levels below)
+  const bool stable = P.stable == kOrderAuto ? l1_auto_ordered(st) : P.stable != 0;
+  const bool in_order = P.in_order == kOrderAuto ? st->l1_ordered != 0 : P.in_order != 0;
+  const bool ordered = stable && in_order;
+  if (P.level == 1 && blockIdx.x == 0 && threadIdx.x == 0) st->l1_ordered = ordered ? 1u : 0u;
   for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
        f += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t g = find_seg(segs, G, f, [](const LevelSeg& x) { return x.bkt_off; });
@@ -1056,9 +1096,6 @@ k_collect(DevState* st, const LevelSeg* segs, const uint64_t* ssk, const uint32_
     }
     if (P.level == 1) atomicMax(&st->max_bucket_l1, size);
     if (!emit_final || size == 0) continue;
-    // buckets keep position order only if the level is stable and its input
-    // was in position order
-    const bool ordered = P.stable && P.in_order;
     bool eq = false;
     if (ordered && b >= 1 && b + 1 < sg.k) {
       const uint64_t klo = ssk[sg.samp_off + ((uint64_t)b * sg.S) / sg.k];
@@ -1571,15 +1608,15 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
                   uint64_t /*n_total*/, int unmap_out, const Overpart* op) {
   const int par_in = P.level & 1;
   const int sms = e.num_sms;
-  static const char* kNames[kMaxLevels + 1][10] = {
+  static const char* kNames[kMaxLevels + 1][11] = {
       {"L?.plan", "L?.sample", "L?.sample_sort", "L?.sample_merge", "L?.classify",
-       "L?.scan_reduce", "L?.scan_sums", "L?.scan_down", "L?.scatter", "L?.collect"},
+       "L?.scan_reduce", "L?.scan_sums", "L?.scan_down", "L?.scatter", "L?.collect", "L?.order"},
       {"L1.plan", "L1.sample", "L1.sample_sort", "L1.sample_merge", "L1.classify",
-       "L1.scan_reduce", "L1.scan_sums", "L1.scan_down", "L1.scatter", "L1.collect"},
+       "L1.scan_reduce", "L1.scan_sums", "L1.scan_down", "L1.scatter", "L1.collect", "L1.order"},
       {"L2.plan", "L2.sample", "L2.sample_sort", "L2.sample_merge", "L2.classify",
-       "L2.scan_reduce", "L2.scan_sums", "L2.scan_down", "L2.scatter", "L2.collect"},
+       "L2.scan_reduce", "L2.scan_sums", "L2.scan_down", "L2.scatter", "L2.collect", "L2.order"},
       {"L3.plan", "L3.sample", "L3.sample_sort", "L3.sample_merge", "L3.classify",
-       "L3.scan_reduce", "L3.scan_sums", "L3.scan_down", "L3.scatter", "L3.collect"}};
+       "L3.scan_reduce", "L3.scan_sums", "L3.scan_down", "L3.scatter", "L3.collect", "L3.order"}};
   const char* const* nm = kNames[(P.level >= 1 && P.level <= kMaxLevels) ? P.level : 0];
   {
     Scope sc(e, nm[0]);
@@ -1613,7 +1650,7 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
       P.chunk_cap, 1,
       sms * (deep_c ? classify_deep_blocks_per_sm((uint32_t)kmax_level, mode)
                     : part_blocks_per_sm((uint32_t)kmax_level, false, mode)));
-  const bool stable = P.stable != 0;
+  const bool stable = P.stable == 1;
   const int grid_s = grid_for(P.chunk_cap, 1,
                               sms * part_blocks_per_sm((uint32_t)kmax_level, true, mode, stable));
   const size_t smem_wd = wd_smem_bytes((uint32_t)kmax_level, mode);
@@ -1641,6 +1678,12 @@ void launch_level(const LaunchEnv& e, const LevelParams& P, DevState* st, const 
   const bool atomics = !units && P.atomic_scatter && !stable && !P.warp_direct &&
                        src.bid != nullptr && atomic_scatter_fits((uint32_t)kmax_level);
   if (!units && !atomics && (P.warp_direct || kmax_level >= 1024)) src.bid = nullptr;
+  // level 1 with its order left to the device: count its equality buckets
+  // (without the unit scatter the level stays unordered)
+  if (units && P.stable == kOrderAuto) {
+    Scope sc(e, nm[10]);
+    k_l1_order<<<grid_for(P.bucket_cap, 256, sms * 4), 256, 0, e.stream>>>(st, segs, ssamp_key);
+  }
   // Deeper levels keep the staged classify below, which stores the ids as
   // well: with many short chunks it measured faster (1.00 vs 1.09 ms at 2^28
   // keys) than the register-streaming one.

@@ -264,25 +264,31 @@ void enqueue_levels_and_local(rsort_ctx* c, Workspace& ws, const Plan& p, const 
                               FinalItem* items, SegIn* const lists[2], rsort_key_type type,
                               const void* d_keys_in, const Dst& out, const Dst& tmp,
                               uint64_t seed, uint32_t k1) {
+  // Level 1 scatters into the output buffer unless the input is that buffer
+  // (an in-place sort): its equality buckets, final when kept in position
+  // order, then need no copy.  Later levels alternate with the scratch
+  // buffer.
+  const int l1_out = (const void*)out.key != d_keys_in ? 1 : 0;
+  auto level_dst = [&](int L) -> const Dst& { return ((L + l1_out) & 1) ? tmp : out; };
   for (int L = 1; L <= p.levels; ++L) {
     const int kmax = L == 1 ? (k1 >= 2 ? (int)k1 : kMaxKDeep) : kMaxKDeep;
     LevelParams P = level_params(p, L, seed, kmax);
-    // level 1 keeps input order inside buckets; deeper levels may not (the
-    // in-SM sort orders (key, position) pairs either way)
-    // a level's input is in position order only after stable levels
+    // the levels keep input order inside buckets or not as the tunables say
+    // (the in-SM sort orders (key, position) pairs either way; level 1's
+    // default leaves it to the device); a level's input is in position order
+    // only after stable levels, and level 1's order is read on the device
     P.stable = L == 1 ? c->level1_stable : c->deep_levels_stable;
-    P.in_order = L == 1 ? 1
-                 : (L == 2 ? c->level1_stable : (c->level1_stable && c->deep_levels_stable));
+    P.in_order = L == 1 ? 1 : (L == 2 || c->deep_levels_stable ? kOrderAuto : 0);
     Src src;
     if (L == 1) {
       src = Src{(const uint64_t*)d_keys_in, nullptr, type == RSORT_KEY_F64};
     } else {
-      const Dst& prev = ((L - 1) & 1) ? tmp : out;
+      const Dst& prev = level_dst(L - 1);
       src = Src{prev.key, prev.idx, 0};
     }
     src.bid = at<uint16_t>(ws, p.off_bid);
-    const Dst& dst = (L & 1) ? tmp : out;
-    const uint16_t where = (L & 1) ? kWhereTmp : kWhereOut;
+    const Dst& dst = level_dst(L);
+    const uint16_t where = &dst == &tmp ? kWhereTmp : kWhereOut;
     launch_level(e, P, st, lists[L & 1], lists[(L + 1) & 1], at<LevelSeg>(ws, p.off_segs), src,
                  dst, where, at<uint64_t>(ws, p.off_samp_key), at<uint32_t>(ws, p.off_samp_idx),
                  at<uint64_t>(ws, p.off_ssamp_key), at<uint32_t>(ws, p.off_ssamp_idx),
@@ -320,7 +326,7 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     return RSORT_OK;
   }
   if (strcmp(name, "level1_stable") == 0) {
-    if (v != 0 && v != 1) return RSORT_EINVAL;
+    if (v != 0 && v != 1 && v != kOrderAuto) return RSORT_EINVAL;
     c->level1_stable = (int)v;
     return RSORT_OK;
   }

@@ -135,7 +135,26 @@ struct DevState {
   uint64_t total_buckets;
   uint64_t big_items;       // buckets that needed the oversize fallback
   uint64_t level_elems[4];  // elements partitioned at levels 1..4
+  // level 1's order (LevelParams::stable == kOrderAuto): equality buckets
+  // among its buckets, its bucket count, and whether its buckets hold their
+  // elements in position order (written by level 1's collect for the levels
+  // after it)
+  uint32_t l1_eq;
+  uint32_t l1_nb;
+  uint32_t l1_ordered;
 };
+
+// LevelParams::stable / in_order value: decided on the device.  Level 1
+// keeps input order when at least 1/kAutoOrderShare of its buckets are
+// equality buckets (copies of one key: kept in position order they are final
+// and skip the levels below), and ranks by atomics otherwise; in_order ==
+// kOrderAuto means "as level 1 left them".
+constexpr int kOrderAuto = 2;
+constexpr uint32_t kAutoOrderShare = 16;
+
+__device__ __forceinline__ bool l1_auto_ordered(const DevState* st) {
+  return st->l1_nb > 0 && (uint64_t)st->l1_eq * kAutoOrderShare >= st->l1_nb;
+}
 
 enum : uint32_t {
   kErrSampleCap = 1u << 0,
@@ -165,11 +184,13 @@ struct LevelParams {
   uint32_t target_by_class[33] = {};
   int no_tie_break = 0;   // 1: classify by key only (the NTB ablation)
   int stable = 1;         // 1: buckets keep input order (the partition step's
-                          // layout); 0: a full sort's deeper level, ranked by
+                          // layout); 0: a full sort's level, ranked by
                           // shared-memory atomics (the in-SM sort orders
-                          // (key, position) pairs, so the result is the same)
+                          // (key, position) pairs, so the result is the same);
+                          // kOrderAuto (level 1 only): decided on the device
   int in_order = 1;       // 1: the level's segments hold their elements in
-                          // position order (level 1, or after a stable level)
+                          // position order (level 1, or after a stable level);
+                          // kOrderAuto: as level 1 left them
   int unit_scatter = 1;   // 1: a stable level with at most kUnitMaxK buckets
                           // stores bucket ids when classifying and scatters
                           // whole 8-element units (unit_scatter.cu)

@@ -474,16 +474,57 @@ __device__ __forceinline__ uint32_t block_excl_max_u32(uint32_t v, uint32_t* sm)
   return excl;
 }
 
+// Ranks every valid element (bucket id != 0xffffffff) of a thread's IT among
+// the elements of its bucket in the sub-tile, in no particular order, by
+// shared-memory atomics on the bucket counters cnt.  Atomics on one word
+// serialise, so runs of one bucket (duplicate-heavy inputs, where the copies
+// of a key fill a bucket by position) are ranked per warp: a warp whose
+// whole window lies in one bucket takes one atomic; a window where lane 0's
+// bucket holds more than 8 lanes of the first round takes one atomic per
+// distinct bucket and round; otherwise every element takes its own.
+template <int IT>
+__device__ __forceinline__ void rank_by_atomics(const uint32_t (&bid)[IT], uint32_t (&rank)[IT],
+                                                uint32_t* cnt, int lane, uint32_t ltmask) {
+  const uint32_t b0 = __shfl_sync(0xffffffffu, bid[0], 0);
+  bool same = b0 != 0xffffffffu;
+#pragma unroll
+  for (int r = 0; r < IT; ++r) same = same && bid[r] == b0;
+  if (__all_sync(0xffffffffu, same)) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&cnt[b0], 32u * IT);
+    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+    for (int r = 0; r < IT; ++r) rank[r] = base + r * 32 + lane;
+  } else if (__popc(__ballot_sync(0xffffffffu, bid[0] == b0)) > 8) {
+#pragma unroll
+    for (int r = 0; r < IT; ++r) {
+      const uint32_t b = bid[r];
+      const uint32_t peers = __match_any_sync(0xffffffffu, b);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (b != 0xffffffffu && lane == leader) base = atomicAdd(&cnt[b], __popc(peers));
+      rank[r] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ltmask);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < IT; ++r)
+      if (bid[r] != 0xffffffffu) rank[r] = atomicAdd(&cnt[bid[r]], 1u);
+  }
+}
+
 // HAS_IDX: the level reads stored positions (deeper levels); otherwise the
 // position is implicit (level 1: offset in the segment).
 // STABLE: elements of a bucket keep input order (ranks from per-warp counters
 // and a prefix over the warps); otherwise (a full sort's level 1, whose
 // buckets the in-SM sort orders by (key, position) anyway) every element takes
 // its rank from one shared-memory atomic on its bucket's counter.
+// auto_order: level 1 with its order decided on the device; the kernel
+// returns at once unless the decision (l1_auto_ordered) is its own form.
 template <int NT, int IT, bool HAS_IDX, bool STABLE>
 __global__ void __launch_bounds__(NT, 1)
 k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_t* hist_scan,
-                Dst dst, uint32_t kmax, int conv, uint32_t aoff) {
+                Dst dst, uint32_t kmax, int conv, uint32_t aoff, bool auto_order) {
+  if (auto_order && l1_auto_ordered(st) != STABLE) return;
   constexpr int NW = NT / 32;
   constexpr int ST = NT * IT;
   static_assert(ST + kUnit < (1 << kMetaUnitShift), "sorted slots fit the meta word");
@@ -593,9 +634,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       //    (unordered: a shared-memory atomic)
       uint32_t lrank[IT];
       if constexpr (!STABLE) {
-#pragma unroll
-        for (int r = 0; r < IT; ++r)
-          if (bid[r] != 0xffffffffu) lrank[r] = atomicAdd(&ucnt[bid[r]], 1u);
+        rank_by_atomics<IT>(bid, lrank, ucnt, lane, ltmask);
       } else {
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
@@ -900,9 +939,7 @@ k_scatter_atomic(const DevState* st, const LevelSeg* segs, Src src, const uint32
         }
       }
       __syncthreads();  // (A) counters cleared, previous sub-tile written out
-#pragma unroll
-      for (int r = 0; r < IT; ++r)
-        if (bid[r] != 0xffffffffu) rank[r] = atomicAdd(&cnt[bid[r]], 1u);
+      rank_by_atomics<IT>(bid, rank, cnt, lane, lanemask_lt());
       __syncthreads();  // (B) counts complete
       {
         uint32_t loc = 0;
@@ -1068,18 +1105,28 @@ void launch_scatter_units(const LaunchEnv& e, const LevelParams& P, DevState* st
   const int g = (int)(grid ? grid : 1);
   const size_t smem_s = us_smem_bytes(kmax, kUsThreads, kUsItems, true);
   const size_t smem_a = us_smem_bytes(kmax, kUsThreadsAny, kUsItemsAny, false);
-  if (src.idx && P.stable)
-    k_scatter_units<kUsThreads, kUsItems, true, true><<<g, kUsThreads, smem_s, e.stream>>>(
-        st, segs, src, hist_scan, dst, kmax, conv, aoff);
-  else if (P.stable)
-    k_scatter_units<kUsThreads, kUsItems, false, true><<<g, kUsThreads, smem_s, e.stream>>>(
-        st, segs, src, hist_scan, dst, kmax, conv, aoff);
-  else if (src.idx)
-    k_scatter_units<kUsThreadsAny, kUsItemsAny, true, false><<<g, kUsThreadsAny, smem_a, e.stream>>>(
-        st, segs, src, hist_scan, dst, kmax, conv, aoff);
-  else
-    k_scatter_units<kUsThreadsAny, kUsItemsAny, false, false><<<g, kUsThreadsAny, smem_a, e.stream>>>(
-        st, segs, src, hist_scan, dst, kmax, conv, aoff);
+  const bool autoo = P.stable == kOrderAuto;
+  if (P.stable == 1 || autoo) {
+    if (src.idx)
+      k_scatter_units<kUsThreads, kUsItems, true, true><<<g, kUsThreads, smem_s, e.stream>>>(
+          st, segs, src, hist_scan, dst, kmax, conv, aoff, autoo);
+    else
+      k_scatter_units<kUsThreads, kUsItems, false, true><<<g, kUsThreads, smem_s, e.stream>>>(
+          st, segs, src, hist_scan, dst, kmax, conv, aoff, autoo);
+  }
+  // with the order left to the device both forms launch; the one not chosen
+  // returns at once
+  if (autoo && e.launches) ++*e.launches;
+  if (P.stable != 1 || autoo) {
+    if (src.idx)
+      k_scatter_units<kUsThreadsAny, kUsItemsAny, true, false>
+          <<<g, kUsThreadsAny, smem_a, e.stream>>>(st, segs, src, hist_scan, dst, kmax, conv,
+                                                   aoff, autoo);
+    else
+      k_scatter_units<kUsThreadsAny, kUsItemsAny, false, false>
+          <<<g, kUsThreadsAny, smem_a, e.stream>>>(st, segs, src, hist_scan, dst, kmax, conv,
+                                                   aoff, autoo);
+  }
 }
 
 }  // namespace rsort

@@ -276,6 +276,7 @@ CONFIGS = {
     "wide_scatter_everywhere": {"classifier": 1, "wide_scatter_k": 2},
     "deep_levels_stable": {"deep_levels_stable": 1, "level1_stable": 1},
     "level1_stable": {"level1_stable": 1},
+    "level1_unordered": {"level1_stable": 0},
     "staged_scatter": {"unit_scatter": 0},
     "atomic_scatter": {"atomic_scatter": 1},
     "bulk_classify": {"bulk_classify": 1},
