@@ -213,18 +213,27 @@ __device__ __forceinline__ void classify_batch_tree(const uint64_t (&x)[R], uint
 
 // Same result through the leading-bits table: one table read per element, then
 // a lower-bound search over the splitters of its bin (usually 0-2 of them).
-template <int R, typename PosFn>
+// PAIRS: elements 2j and 2j+1 sit at consecutive positions whenever
+// valid(2j) and valid(2j+1); when both tie with the same run of splitter keys,
+// the second element's bucket is the first's or the next (splitter positions
+// are distinct, so at most one more of them lies below it): one comparison
+// instead of a search.
+template <int R, bool PAIRS = false, typename PosFn, typename ValidFn>
 __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uint32_t (&b)[R],
-                                                     PosFn pos_of, const Splitters& sp) {
+                                                     PosFn pos_of, ValidFn valid,
+                                                     const Splitters& sp) {
   uint32_t pr[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const bool inside = x[r] >= sp.lo && x[r] <= sp.hi;
     pr[r] = inside ? sp.tbl[(uint32_t)((x[r] - sp.lo) >> sp.shift)] : 0u;
   }
+  bool prev_tied = false;
+  uint32_t prev_b = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     uint32_t bb;
+    bool tied = false;
     if (x[r] < sp.lo || sp.nspl == 0) {
       bb = 0;
     } else if (x[r] > sp.hi) {
@@ -255,9 +264,19 @@ __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uin
         }
       }
       bb = lo;
-      if (!sp.ntb && bb < end && ub == x[r]) bb = tie_break(bb, x[r], pos_of(r), sp);
+      tied = !sp.ntb && bb < end && ub == x[r];
+      if (tied) {
+        if (PAIRS && (r & 1) && prev_tied && x[r] == x[r - 1] && valid(r - 1) && valid(r)) {
+          const uint32_t re = sp.rend[bb];
+          bb = prev_b + (prev_b < re && sp.idx[prev_b] < pos_of(r) ? 1u : 0u);
+        } else {
+          bb = tie_break(bb, x[r], pos_of(r), sp);
+        }
+      }
     }
     b[r] = bb;
+    prev_tied = tied;
+    prev_b = bb;
   }
 }
 
@@ -265,7 +284,17 @@ template <int R, typename PosFn>
 __device__ __forceinline__ void classify_batch(const uint64_t (&x)[R], uint32_t (&b)[R],
                                                PosFn pos_of, const Splitters& sp) {
   if (sp.mode == 0) classify_batch_tree<R>(x, b, pos_of, sp);
-  else classify_batch_table<R>(x, b, pos_of, sp);
+  else classify_batch_table<R>(x, b, pos_of, [](int) { return false; }, sp);
+}
+
+// The same for elements in consecutive-position pairs (see
+// classify_batch_table); valid(e) says whether element e is a real element.
+template <int R, typename PosFn, typename ValidFn>
+__device__ __forceinline__ void classify_batch_pairs(const uint64_t (&x)[R], uint32_t (&b)[R],
+                                                     PosFn pos_of, ValidFn valid,
+                                                     const Splitters& sp) {
+  if (sp.mode == 0) classify_batch_tree<R>(x, b, pos_of, sp);
+  else classify_batch_table<R, true>(x, b, pos_of, valid, sp);
 }
 
 

@@ -172,10 +172,17 @@ k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t
       uint32_t bk[R];
       // positions are read only on a key tie, and only inside the chunk (a
       // padding slot's result is discarded)
-      classify_batch<R>(key, bk, [&](int e) {
-        const uint64_t pos = ps + 2 * (p0 + (uint64_t)(e >> 1) * NT + threadIdx.x) + (e & 1);
+      // (each thread's elements come in pairs of consecutive positions)
+      auto pos_at = [&](int e) {
+        return ps + 2 * (p0 + (uint64_t)(e >> 1) * NT + threadIdx.x) + (e & 1);
+      };
+      classify_batch_pairs<R>(key, bk, [&](int e) {
+        const uint64_t pos = pos_at(e);
         if (pos < cs || pos >= ce) return 0u;
         return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
+      }, [&](int e) {
+        const uint64_t pos = pos_at(e);
+        return pos >= cs && pos < ce && src.idx == nullptr;
       }, sp);
 #pragma unroll
       for (int r = 0; r < kCiPairs; ++r) {
@@ -638,6 +645,18 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
       } else {
       for (uint32_t q = lane; q < (k + 1) / 2; q += 32) ((uint32_t*)my_cnt)[q] = 0;
       __syncwarp();
+      // a warp whose whole window lies in one bucket (runs of copies of a
+      // key) ranks its elements by their place in the window
+      const uint32_t b0 = __shfl_sync(0xffffffffu, bid[0], 0);
+      bool same = b0 != 0xffffffffu;
+#pragma unroll
+      for (int r = 0; r < IT; ++r) same = same && bid[r] == b0;
+      if (__all_sync(0xffffffffu, same)) {
+#pragma unroll
+        for (int r = 0; r < IT; ++r) lrank[r] = r * 32 + lane;
+        if (lane == 0) my_cnt[b0] = (uint16_t)(32 * IT);
+        __syncwarp();
+      } else {
 #pragma unroll
       for (int r = 0; r < IT; ++r) {
         const uint32_t b = bid[r];
@@ -673,6 +692,7 @@ k_scatter_units(const DevState* st, const LevelSeg* segs, Src src, const uint32_
         __syncwarp();
         lrank[r] = c0 + __popc(peers & ltmask);
       }
+      }  // mixed window
       }  // STABLE
       __syncthreads();  // (A) every warp's counts are in
       // -- 2. per bucket: exclusive prefix over the warps' counts (in place),
