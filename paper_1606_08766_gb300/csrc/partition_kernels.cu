@@ -487,9 +487,13 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
         key[r] = src.map_f64 ? f64_to_ordered(k) : k;
       }
       uint32_t bk[kCItems];
-      // positions are read only when a key ties with a splitter key
+      // positions are read only when a key ties with a splitter key, and
+      // never past the stage (a padding slot's key 0 may tie; its result is
+      // discarded)
       classify_batch<kCItems>(key, bk, [&](int r) {
-        const uint64_t pos = b0 + q0 + r * 32;
+        const uint32_t q = q0 + r * 32;
+        if (q >= len) return 0u;
+        const uint64_t pos = b0 + q;
         return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
       }, sm.sp);
       if (src.bid) {
@@ -925,8 +929,10 @@ k_classify_count_wd(const DevState* st, const LevelSeg* segs, Src src, const uin
         key[r] = src.map_f64 ? f64_to_ordered(kv) : kv;
       }
       uint32_t bk[kWdItems];
+      // (never past the sub-chunk: a padding slot's result is discarded)
       classify_batch<kWdItems>(key, bk, [&](int r) {
         const uint64_t pos = b0 + r * 32 + lane;
+        if (pos >= we) return 0u;
         return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
       }, sm.sp);
 #pragma unroll
