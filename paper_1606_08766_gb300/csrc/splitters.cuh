@@ -61,6 +61,7 @@ struct Splitters {
   uint64_t lo, hi;  // smallest / largest splitter key
   int logK;         // log2(Kp)
   int tbits;        // table bits
+  uint32_t tmax;    // last table entry (2^tbits - 1)
   int shift;        // key bits dropped before the table index
   int mode;         // 0 tree, 1 table
   int ntb;          // 1: no tie-breaking, classify by key only (ablation)
@@ -111,6 +112,7 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
     sp.tbits = table_bits_for(Kp);
     sp.shift = bits > sp.tbits ? bits - sp.tbits : 0;
     const uint32_t T = 1u << sp.tbits;
+    sp.tmax = T - 1;
     // first splitter whose bin is >= t, by binary search over the sorted keys
     auto first_at_least = [&](uint32_t t) {
       uint32_t lo = 0, hi = sp.nspl;
@@ -123,10 +125,13 @@ __device__ void load_splitters(const LevelSeg& sg, const uint64_t* ssk, const ui
     for (uint32_t t = threadIdx.x; t < T; t += NT)
       sp.tbl[t] = first_at_least(t) | (first_at_least(t + 1) << 16);
   } else {
-    sp.lo = ~0ULL;
+    // no splitters: one bin, empty, so every key lands in bucket 0
+    sp.lo = 0;
     sp.hi = 0;
     sp.tbits = 0;
+    sp.tmax = 0;
     sp.shift = 0;
+    if (threadIdx.x == 0) sp.tbl[0] = 0;
   }
   __syncthreads();
 }
@@ -222,11 +227,14 @@ template <int R, bool PAIRS = false, typename PosFn, typename ValidFn>
 __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uint32_t (&b)[R],
                                                      PosFn pos_of, ValidFn valid,
                                                      const Splitters& sp) {
+  // A key below the smallest splitter reads bin 0 and one above the largest
+  // the last bin: each then finds no splitter on its far side, so no case
+  // needs its own branch.
   uint32_t pr[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const bool inside = x[r] >= sp.lo && x[r] <= sp.hi;
-    pr[r] = inside ? sp.tbl[(uint32_t)((x[r] - sp.lo) >> sp.shift)] : 0u;
+    const uint64_t t = (x[r] > sp.lo ? x[r] - sp.lo : 0ull) >> sp.shift;
+    pr[r] = sp.tbl[t < sp.tmax ? (uint32_t)t : sp.tmax];
   }
   bool prev_tied = false;
   uint32_t prev_b = 0;
@@ -234,11 +242,7 @@ __device__ __forceinline__ void classify_batch_table(const uint64_t (&x)[R], uin
   for (int r = 0; r < R; ++r) {
     uint32_t bb;
     bool tied = false;
-    if (x[r] < sp.lo || sp.nspl == 0) {
-      bb = 0;
-    } else if (x[r] > sp.hi) {
-      bb = sp.nspl;
-    } else {
+    {
       uint32_t lo = pr[r] & 0xffffu, hi = pr[r] >> 16;
       const uint32_t end = hi;
       uint64_t ub = ~0ULL;
