@@ -106,18 +106,26 @@ __device__ __forceinline__ void cta_bitonic_pairs(const uint64_t (&key)[ITEMS],
   block_bitonic_sort<NT>(s.k, s.i, (int)P);
 }
 
+// No-op for cta_sort_pairs' released callback.
+struct NoRelease {
+  __device__ void operator()() const {}
+};
+
 // Sorts the m pairs; on return s.k[0..m) / s.i[0..m) hold them in order.
 // in_position_order() says whether the elements arrive with increasing
 // positions; it is asked only when all keys are equal.  algo (nullable) gets
 // m added to the counter of the branch taken (kAlgoRank, kAlgoInOrder,
 // kAlgoBitonic or kAlgoBins).  rank_max bounds rank-by-counting (at most NT
 // elements: one per thread); force_bitonic sorts every larger bucket by
-// bitonic sort instead of the bins.
-template <int NT, int ITEMS, typename InOrderFn>
+// bitonic sort instead of the bins.  released() is called once by every
+// thread of the CTA, together, as soon as key[] and idx[] are no longer read
+// (the pairs are in shared memory): the caller may then load the next
+// bucket into them while this one is finished.
+template <int NT, int ITEMS, typename InOrderFn, typename ReleaseFn = NoRelease>
 __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], uint32_t m,
                                InOrderFn in_position_order, const CtaSortSmem& s, uint64_t* red,
                                uint64_t* scan_sm, uint64_t* algo, uint32_t rank_max = kRankMax,
-                               bool force_bitonic = false) {
+                               bool force_bitonic = false, ReleaseFn released = ReleaseFn()) {
   constexpr uint32_t kCap = NT * ITEMS;
   static_assert(ITEMS >= 4, "the padded counters need cap/4 >= NT words of slack");
   const uint32_t tid = threadIdx.x;
@@ -136,11 +144,13 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     __syncthreads();
     if (tid < m) { s.k[rank] = key[0]; s.i[rank] = idx[0]; }
     __syncthreads();
+    released();
     return;
   }
   if (force_bitonic) {
     count_algo(algo, kAlgoBitonic, m);
     cta_bitonic_pairs<NT, ITEMS>(key, idx, m, s);
+    released();
     return;
   }
   uint64_t mn = ~0ULL, mx = 0;
@@ -160,6 +170,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
       if (e < m) { s.k[e] = key[r]; s.i[e] = idx[r]; }
     }
     __syncthreads();
+    released();
     return;
   }
   // all keys equal, in no particular order: (key, position) order is the
@@ -236,6 +247,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     count_algo(algo, kAlgoBitonic, m);
     cta_bitonic_pairs<NT, ITEMS>(key, idx, m, s);
     restore_common_key<NT>(s, m, s_by_pos, s_key_all);
+    released();
     return;
   }
   // counting-sort scatter into the bins; the second element to land in a bin
@@ -253,6 +265,7 @@ __device__ void cta_sort_pairs(uint64_t (&key)[ITEMS], uint32_t (&idx)[ITEMS], u
     }
   }
   __syncthreads();
+  released();
   // order every listed bin in place by insertion (at most kBinLimit elements;
   // an element alone in its bin is already in its final slot)
   const uint32_t nmulti = s_nmulti;

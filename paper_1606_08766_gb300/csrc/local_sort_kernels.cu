@@ -190,15 +190,27 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
     load_bucket<NT, IT>(B, f, key, idx);
   }
   while (it >= 0) {
-    cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
-                           red, scan_sm, st->algo_elems, rank_max, bitonic);
-    // claim and start loading the next bucket before this one is stored, so
-    // its loads are in flight while the stores go out
-    const int64_t it2 = next_item(st, CLS, cap, &s_item);
+    // claim the next bucket and start loading it into the registers as soon
+    // as this one's pairs sit in shared memory (the classes above the small
+    // one, whose buckets take long enough to finish), else after sorting, so
+    // its loads are in flight while this one is finished and stored (the
+    // small class has too few registers to hold the claim across the sort)
+    int64_t it2 = -1;
     FinalItem f2{};
-    if (it2 >= 0) {
-      f2 = list[it2];
-      load_bucket<NT, IT>(B, f2, key, idx);
+    auto claim_next = [&] {
+      it2 = next_item(st, CLS, cap, &s_item);
+      if (it2 >= 0) {
+        f2 = list[it2];
+        load_bucket<NT, IT>(B, f2, key, idx);
+      }
+    };
+    if constexpr (CLS == kClassSmall) {
+      cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
+                             red, scan_sm, st->algo_elems, rank_max, bitonic);
+      claim_next();
+    } else {
+      cta_sort_pairs<NT, IT>(key, idx, f.size, [&] { return list[it].kind == kKindSort; }, s,
+                             red, scan_sm, st->algo_elems, rank_max, bitonic, claim_next);
     }
     for (uint32_t t = threadIdx.x; t < f.size; t += NT) store_out(B, f.start + t, s.k[t], s.i[t]);
     __syncthreads();
