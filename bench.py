@@ -580,12 +580,21 @@ def run_rsort(args):
         kernels[name] = info
     dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["ms_per_launch"]
               * kernels[k]["launches"])
-    traffic = MEASURED_TRAFFIC_PER_KEY.get(dom)
-    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak,
-            "unit": "GB/s", "frac": kernels[dom]["gbs"] / peak, "peak_kind": peak_kind,
-            "algo_bytes_per_launch": kernels[dom]["algo_bytes"],
-            "traffic": (traffic * elems.get(dom.split(".")[0] if "." in dom else dom, n)
-                        if traffic else None)}
+
+    def roofline_of(name):
+        t = MEASURED_TRAFFIC_PER_KEY.get(name)
+        return {"kernel": name, "bound": "hbm", "achieved": kernels[name]["gbs"], "peak": peak,
+                "unit": "GB/s", "frac": kernels[name]["gbs"] / peak, "peak_kind": peak_kind,
+                "algo_bytes_per_launch": kernels[name]["algo_bytes"],
+                "traffic": (t * elems.get(name.split(".")[0] if "." in name else name, n)
+                            if t else None)}
+
+    roof = roofline_of(dom)
+    # the same entry for every kernel with algorithmic bytes (classify and
+    # scatter of each level, the in-SM sort classes), largest first
+    rooflines = [roofline_of(k) for k in sorted(
+        (k for k in kernels if "gbs" in kernels[k]),
+        key=lambda k: -kernels[k]["ms_per_launch"] * kernels[k]["launches"])]
 
     # -- end to end through the C ABI with host buffers (pinned): every step
     # copies its input up and its result (keys + permutation) down, inside the
@@ -694,7 +703,7 @@ def run_rsort(args):
                        "max_over_mean": st.max_over_mean, "levels": st.levels,
                        "tunables": {"classifier": ctx.get_tunable("classifier")}},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "kernels": kernels, **extra,
+            "gpu_launches": launches, "rooflines": rooflines, "kernels": kernels, **extra,
         }))
     ctx.close()
     if dist:
