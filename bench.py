@@ -52,11 +52,11 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    "L1.scatter": 23.65,       # 0.7691 + 0.8181 GB at 2^26 keys (k_scatter_units<512,12,0,0>)
-    "L1.classify": 9.45,       # 0.5449 + 0.0893 GB (k_classify_ids, ids included)
-    "L2.scatter": 25.39,       # 0.9530 + 0.7510 GB (k_scatter_units<512,12,1,0>)
-    "L2.classify": 9.39,       # 0.5519 + 0.0783 GB (k_classify_count<2>)
-    "local_sort_mid": 23.02,   # 0.6677 + 0.6053 GB over 55.3 M keys of the class
+    "L1.scatter": 23.66,       # 0.7693 + 0.8185 GB at 2^26 keys (k_scatter_units<512,12,0,0>)
+    "L1.classify": 9.44,       # 0.5450 + 0.0886 GB (k_classify_ids, ids included)
+    "L2.scatter": 25.35,       # 0.9511 + 0.7504 GB (k_scatter_units<512,12,1,0>)
+    "L2.classify": 9.38,       # 0.5518 + 0.0780 GB (k_classify_count<2>)
+    "local_sort_mid": 23.11,   # 0.6687 + 0.6140 GB over 55.5 M keys of the class
 }
 
 
