@@ -258,8 +258,25 @@ def config1_leg(ctx, dev, n=1 << 20, p=64, reps=20):
     for _ in range(3):
         fn()
     ms = _event_ms(fn, stream, reps)
+    ref_k, ref_p = ko.clone(), po.clone()
+    # the same call's ~30 launches captured once in a CUDA graph and replayed
+    # (the launch sequence of a sort this small costs about what its kernels do)
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        ctx.sort(keys, p=p, keys_out=ko, perm_out=po, stream=side)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ctx.sort(keys, p=p, keys_out=ko, perm_out=po, stream=side)
+    ko.zero_()
+    po.zero_()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    same = bool(torch.equal(ko, ref_k)) and bool(torch.equal(po, ref_p))
+    ms_graph = _event_ms(g.replay, stream, reps)
     return {"workload": f"Uniform uint64 keys, n=2^20, p={p}, seed 1", "ms": ms,
-            "gkeys_s": n / (ms / 1e3) / 1e9}
+            "gkeys_s": n / (ms / 1e3) / 1e9, "graph_replay_ms": ms_graph,
+            "graph_replay_gkeys_s": n / (ms_graph / 1e3) / 1e9, "graph_identical": same}
 
 
 def instances_leg(ctx, dev, n=1 << 28, p=1024, reps=3):

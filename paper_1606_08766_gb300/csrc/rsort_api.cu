@@ -830,12 +830,14 @@ rsort_status rsort_sort(rsort_ctx* c, rsort_key_type type, const void* d_keys_in
     opt_stats->max_over_mean = mean > 0 ? opt_stats->max_bucket / mean : 0.0;
     opt_stats->final_buckets = 0;
     for (int i = 0; i < kNumClasses; ++i) opt_stats->final_buckets += h.nfinal_c[i];
-    // level 1 reads 8 B/key twice and writes 12; deeper levels read 8 + 12 and
-    // write 12; the in-SM sort reads and writes 12 B/key.
+    // per key: level 1's classify reads 8 B and writes a 2-byte bucket id,
+    // its scatter reads 8 + 2 and writes 12; a deeper level reads 8 and
+    // writes 2, then reads 12 + 2 and writes 12; the in-SM sort reads and
+    // writes 12 B/key.
     uint64_t bytes = 24ull * n;
     for (int i = 0; i < 4; ++i) {
       opt_stats->level_elems[i] = h.level_elems[i];
-      bytes += (i == 0 ? 28ull : 32ull) * h.level_elems[i];
+      bytes += (i == 0 ? 32ull : 36ull) * h.level_elems[i];
     }
     opt_stats->bytes_moved = bytes;
     static_assert(kNumClasses == 5, "rsort_stats.class_elems has one entry per size class");

@@ -336,3 +336,32 @@ def test_tunable_rejects_unknown(ctx):
         ctx.set_tunable("no_such_knob", 1)
     with pytest.raises(RsortError):
         ctx.set_tunable("classifier", 7)
+
+
+@pytest.mark.parametrize("name", ["uniform", "zero"])
+def test_sort_replayed_from_cuda_graph(oracle_mod, name):
+    # rsort_sort enqueues without host synchronisation once its scratch is
+    # sized, so a caller can capture a sort in a CUDA graph and replay it on
+    # new keys of the same size (config 1's launch-bound size)
+    from paper_1606_08766_gb300 import Context
+    n = 1 << 20
+    keys = instances.generate(name, n, p=64, seed=9)
+    x = _dev(keys)
+    ko = torch.empty_like(x)
+    po = torch.empty(n, dtype=torch.int32, device="cuda")
+    with Context(0) as c:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            c.sort(x, p=64, keys_out=ko, perm_out=po, stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            c.sort(x, p=64, keys_out=ko, perm_out=po, stream=s)
+        keys2 = instances.generate("uniform", n, p=64, seed=10)
+        x.copy_(_dev(keys2))
+        g.replay()
+        torch.cuda.synchronize()
+        rk, rp = oracle_mod.sort(keys2)
+        np.testing.assert_array_equal(_host_u32(po), rp)
+        np.testing.assert_array_equal(_host_u64(ko), rk)
+        c.check()
