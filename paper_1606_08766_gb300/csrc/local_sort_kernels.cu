@@ -159,6 +159,22 @@ __device__ __forceinline__ int64_t next_item(DevState* st, int cls, uint64_t cap
   return it < umin64(st->nfinal_c[cls], cap) ? (int64_t)it : -1;
 }
 
+// The same in two steps: claim_item() sends the atomic (thread 0 keeps its
+// result in a register, so nothing waits for it), take_item() publishes the
+// claimed item to the CTA later, after the atomic's round trip has passed in
+// other work.
+__device__ __forceinline__ uint32_t claim_item(DevState* st, int cls) {
+  return threadIdx.x == 0 ? atomicAdd(&st->cursor_c[cls], 1u) : 0u;
+}
+__device__ __forceinline__ int64_t take_item(const DevState* st, int cls, uint64_t cap,
+                                             uint32_t claimed, uint32_t* s_item) {
+  if (threadIdx.x == 0) *s_item = claimed;
+  __syncthreads();
+  const uint32_t it = *s_item;
+  __syncthreads();
+  return it < umin64(st->nfinal_c[cls], cap) ? (int64_t)it : -1;
+}
+
 // Resident CTAs per SM of the small class: the sort is latency-bound per
 // bucket, so more buckets in flight per SM pay more than registers (10 CTAs
 // of 128 threads measured 17% faster than 6 at 2^28 keys).
@@ -190,15 +206,17 @@ k_local_sort(DevState* st, const FinalItem* items, uint64_t cap, Bufs B) {
     load_bucket<NT, IT>(B, f, key, idx);
   }
   while (it >= 0) {
-    // claim the next bucket and start loading it into the registers as soon
-    // as this one's pairs sit in shared memory (the classes above the small
-    // one, whose buckets take long enough to finish), else after sorting, so
-    // its loads are in flight while this one is finished and stored (the
-    // small class has too few registers to hold the claim across the sort)
+    // the next bucket is claimed now (the atomic's round trip passes during
+    // this sort) and loaded into the registers as soon as this one's pairs
+    // sit in shared memory (the classes above the small one, whose buckets
+    // take long enough to finish), else after sorting, so its loads are in
+    // flight while this one is finished and stored (the small class has too
+    // few registers to hold the claim across the sort)
+    const uint32_t claimed = claim_item(st, CLS);
     int64_t it2 = -1;
     FinalItem f2{};
     auto claim_next = [&] {
-      it2 = next_item(st, CLS, cap, &s_item);
+      it2 = take_item(st, CLS, cap, claimed, &s_item);
       if (it2 >= 0) {
         f2 = list[it2];
         load_bucket<NT, IT>(B, f2, key, idx);
