@@ -88,10 +88,12 @@ constexpr int kCiPairs = 4;  // 16-byte loads (two keys) per thread per step
 // the next step's keys are already in registers)
 constexpr int kCiPrefetch = 2;
 
-template <int NT>
+// VEC: the key array is 16-byte aligned (pairs are read by 16-byte loads);
+// MAP: the keys are float64 bit patterns, mapped to the order map on load.
+template <int NT, bool VEC, bool MAP>
 __global__ void __launch_bounds__(NT, 3)
 k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t* ssk,
-               const uint32_t* ssi, uint32_t* hist, uint32_t kmax, int mode, int vec) {
+               const uint32_t* ssi, uint32_t* hist, uint32_t kmax, int mode) {
   constexpr int R = 2 * kCiPairs;  // keys per thread per step
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Splitters sp;
@@ -134,19 +136,26 @@ k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t
     const uint64_t cs = sg.start + cl * sg.W;
     const uint64_t ce = umin64(cs + sg.W, sg.start + sg.m);
     // pairs start at the even position at or below cs (16-byte aligned when
-    // the key array is); a pair reaches past ce only by its second element
+    // the key array is).  VEC: every pair wholly before ce is read by one
+    // 16-byte load, from a position clamped into that range (pairs past it
+    // read a valid pair and discard it), so the loop has no load branch; an
+    // odd chunk end's last key is handled after the loop.  Otherwise every
+    // key is read by its own checked load.
     const uint64_t ps = cs & ~1ull;
-    const uint64_t npairs = (ce - ps + 1) >> 1;
+    const uint64_t npairs = VEC ? (ce - ps) >> 1 : (ce - ps + 1) >> 1;
     auto load = [&](uint64_t p0, uint64_t (&x)[R]) {
 #pragma unroll
       for (int r = 0; r < kCiPairs; ++r) {
         const uint64_t j = p0 + (uint64_t)r * NT + threadIdx.x;
-        const uint64_t pos = ps + 2 * j;
-        x[2 * r] = x[2 * r + 1] = 0;
-        if (j < npairs) {
-          if (vec && pos + 1 < ce) {
-            ld_stream_v2(x[2 * r], x[2 * r + 1], src.key + pos, pol);
-          } else {
+        if constexpr (VEC) {
+          uint64_t a, b;
+          ld_stream_v2(a, b, src.key + ps + 2 * (j < npairs ? j : npairs - 1), pol);
+          x[2 * r] = j < npairs ? a : 0;
+          x[2 * r + 1] = j < npairs ? b : 0;
+        } else {
+          const uint64_t pos = ps + 2 * j;
+          x[2 * r] = x[2 * r + 1] = 0;
+          if (j < npairs) {
             x[2 * r] = ld_stream_u64(src.key + pos, pol);
             if (pos + 1 < ce) x[2 * r + 1] = ld_stream_u64(src.key + pos + 1, pol);
           }
@@ -162,13 +171,13 @@ k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t
     };
     for (int d = 2; d < kCiPrefetch; ++d) prefetch((uint64_t)d * NT * kCiPairs);
     uint64_t x[R], xn[R];
-    load(0, x);
+    if (npairs > 0) load(0, x);
     for (uint64_t p0 = 0; p0 < npairs; p0 += (uint64_t)NT * kCiPairs) {
       prefetch(p0 + (uint64_t)kCiPrefetch * NT * kCiPairs);
       load(p0 + (uint64_t)NT * kCiPairs, xn);
       uint64_t key[R];
 #pragma unroll
-      for (int e = 0; e < R; ++e) key[e] = src.map_f64 ? f64_to_ordered(x[e]) : x[e];
+      for (int e = 0; e < R; ++e) key[e] = MAP ? f64_to_ordered(x[e]) : x[e];
       uint32_t bk[R];
       // positions are read only on a key tie, and only inside the chunk (a
       // padding slot's result is discarded)
@@ -176,41 +185,69 @@ k_classify_ids(const DevState* st, const LevelSeg* segs, Src src, const uint64_t
       auto pos_at = [&](int e) {
         return ps + 2 * (p0 + (uint64_t)(e >> 1) * NT + threadIdx.x) + (e & 1);
       };
+      auto valid = [&](int e) {
+        const uint64_t pos = pos_at(e);
+        return (p0 + (uint64_t)(e >> 1) * NT + threadIdx.x) < npairs && pos >= cs && pos < ce;
+      };
       classify_batch_pairs<R>(key, bk, [&](int e) {
+        if (!valid(e)) return 0u;
         const uint64_t pos = pos_at(e);
-        if (pos < cs || pos >= ce) return 0u;
         return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
-      }, [&](int e) {
-        const uint64_t pos = pos_at(e);
-        return pos >= cs && pos < ce && src.idx == nullptr;
-      }, sp);
+      }, [&](int e) { return valid(e) && src.idx == nullptr; }, sp);
+      // a step whose pairs all lie inside the chunk stores them whole
+      const bool whole = ps == cs && p0 + (uint64_t)NT * kCiPairs <= npairs &&
+                         ps + 2 * (p0 + (uint64_t)NT * kCiPairs) <= ce;
+      // runs of one bucket across the warp (duplicate-heavy inputs) take one
+      // atomic per warp and slot; otherwise one atomic per key
+      const uint32_t b0 = __shfl_sync(0xffffffffu, bk[0], 0);
+      const bool skewed = __popc(__ballot_sync(0xffffffffu, bk[0] == b0)) > 8;
+      uint32_t vmask = 0;  // valid elements of the step
 #pragma unroll
       for (int r = 0; r < kCiPairs; ++r) {
         const uint64_t j = p0 + (uint64_t)r * NT + threadIdx.x;
         const uint64_t pos = ps + 2 * j;
-        const bool v0 = j < npairs && pos >= cs;
-        const bool v1 = j < npairs && pos + 1 < ce;
-        if (v0 && v1) {
+        const bool v0 = whole || (j < npairs && pos >= cs && pos < ce);
+        const bool v1 = whole || (j < npairs && pos + 1 < ce);
+        if (whole || (v0 && v1)) {
           *reinterpret_cast<uint32_t*>(src.bid + pos) = bk[2 * r] | (bk[2 * r + 1] << 16);
         } else if (v0) {
           src.bid[pos] = (uint16_t)bk[2 * r];
         } else if (v1) {
           src.bid[pos + 1] = (uint16_t)bk[2 * r + 1];
         }
+        vmask |= ((v0 ? 1u : 0u) | (v1 ? 2u : 0u)) << (2 * r);
+      }
+      if (!skewed) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const bool v = h ? v1 : v0;
-          const uint32_t b = bk[2 * r + h];
-          const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
-          if (__all_sync(0xffffffffu, v && b == bl)) {
+        for (int e = 0; e < R; ++e)
+          if ((vmask >> e) & 1u) atomicAdd(&cnt[bk[e]], 1u);
+      } else {
+#pragma unroll
+        for (int e = 0; e < R; ++e) {
+          const bool v = (vmask >> e) & 1u;
+          const uint32_t bl = __shfl_sync(0xffffffffu, bk[e], 0);
+          if (__all_sync(0xffffffffu, v && bk[e] == bl)) {
             if (lane == 0) atomicAdd(&cnt[bl], 32u);
           } else if (v) {
-            atomicAdd(&cnt[b], 1u);
+            atomicAdd(&cnt[bk[e]], 1u);
           }
         }
       }
 #pragma unroll
       for (int e = 0; e < R; ++e) x[e] = xn[e];
+    }
+    // VEC: an odd chunk end's last key (the pair it starts would read one key
+    // past the chunk)
+    if (VEC && threadIdx.x == 0 && ((ce - ps) & 1) && ce - 1 >= cs) {
+      const uint64_t pos = ce - 1;
+      const uint64_t raw = ld_stream_u64(src.key + pos, pol);
+      uint64_t k1[1] = {MAP ? f64_to_ordered(raw) : raw};
+      uint32_t b1[1];
+      classify_batch<1>(k1, b1, [&](int) {
+        return src.idx ? src.idx[pos] : (uint32_t)(pos - sg.start);
+      }, sp);
+      src.bid[pos] = (uint16_t)b1[0];
+      atomicAdd(&cnt[b1[0]], 1u);
     }
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < sg.k; b += NT)
@@ -1020,9 +1057,16 @@ bool unit_scatter_fits(uint32_t kmax) {
 }
 
 void set_unit_scatter_attributes() {
-  cudaFuncSetAttribute(k_classify_ids<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)umax64(classify_ids_smem_bytes(kMaxK, 0),
-                                   classify_ids_smem_bytes(kMaxK, 1)));
+  const int ci_smem = (int)umax64(classify_ids_smem_bytes(kMaxK, 0),
+                                  classify_ids_smem_bytes(kMaxK, 1));
+  cudaFuncSetAttribute(k_classify_ids<256, true, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
+  cudaFuncSetAttribute(k_classify_ids<256, true, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
+  cudaFuncSetAttribute(k_classify_ids<256, false, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
+  cudaFuncSetAttribute(k_classify_ids<256, false, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
   cudaFuncSetAttribute(k_classify_bulk<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)classify_bulk_smem_bytes(umax64(classify_ids_smem_bytes(kMaxK, 0),
                                                             classify_ids_smem_bytes(kMaxK, 1))));
@@ -1077,14 +1121,26 @@ void launch_classify_ids(const LaunchEnv& e, const LevelParams& P, DevState* st,
   }
   const size_t smem = classify_ids_smem_bytes(kmax, mode);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_ids<256>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_classify_ids<256, true, false>, 256,
+                                                smem);
   if (nb < 1) nb = 1;
   const uint64_t grid = umin64(P.chunk_cap, (uint64_t)e.num_sms * nb);
   // 16-byte pair loads need a 16-byte aligned key array
   const int vec = ((uintptr_t)src.key & 15) == 0;
   Scope sc(e, name);
-  k_classify_ids<256><<<(int)(grid ? grid : 1), 256, smem, e.stream>>>(st, segs, src, ssk, ssi,
-                                                                       hist, kmax, mode, vec);
+  const int g = (int)(grid ? grid : 1);
+  if (vec && src.map_f64)
+    k_classify_ids<256, true, true><<<g, 256, smem, e.stream>>>(st, segs, src, ssk, ssi, hist,
+                                                                kmax, mode);
+  else if (vec)
+    k_classify_ids<256, true, false><<<g, 256, smem, e.stream>>>(st, segs, src, ssk, ssi, hist,
+                                                                 kmax, mode);
+  else if (src.map_f64)
+    k_classify_ids<256, false, true><<<g, 256, smem, e.stream>>>(st, segs, src, ssk, ssi, hist,
+                                                                 kmax, mode);
+  else
+    k_classify_ids<256, false, false><<<g, 256, smem, e.stream>>>(st, segs, src, ssk, ssi, hist,
+                                                                  kmax, mode);
 }
 
 void launch_scatter_atomic(const LaunchEnv& e, const LevelParams& P, DevState* st,
