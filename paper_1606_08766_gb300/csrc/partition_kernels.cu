@@ -501,16 +501,25 @@ k_classify_count(const DevState* st, const LevelSeg* segs, Src src, const uint64
         for (int r = 0; r < kCItems; ++r)
           if (q0 + r * 32 < len) src.bid[b0 + q0 + r * 32] = (uint16_t)bk[r];
       }
+      // runs of one bucket across the warp (duplicate-heavy inputs) take one
+      // atomic per warp and slot; otherwise one atomic per key
+      const uint32_t bw = __shfl_sync(0xffffffffu, bk[0], 0);
+      if (__popc(__ballot_sync(0xffffffffu, bk[0] == bw)) > 8) {
 #pragma unroll
-      for (int r = 0; r < kCItems; ++r) {
-        const bool v = q0 + r * 32 < len;
-        const uint32_t b = bk[r];
-        const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
-        if (__all_sync(0xffffffffu, v && b == bl)) {
-          if (lane == 0) atomicAdd(&sm.hist[bl], 32u);
-        } else if (v) {
-          atomicAdd(&sm.hist[b], 1u);
+        for (int r = 0; r < kCItems; ++r) {
+          const bool v = q0 + r * 32 < len;
+          const uint32_t b = bk[r];
+          const uint32_t bl = __shfl_sync(0xffffffffu, b, 0);
+          if (__all_sync(0xffffffffu, v && b == bl)) {
+            if (lane == 0) atomicAdd(&sm.hist[bl], 32u);
+          } else if (v) {
+            atomicAdd(&sm.hist[b], 1u);
+          }
         }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kCItems; ++r)
+          if (q0 + r * 32 < len) atomicAdd(&sm.hist[bk[r]], 1u);
       }
     }
     cp_async_wait<0>();
