@@ -328,11 +328,13 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                buckets; 0 (default): they rank elements by shared-memory
  *                atomics.  The result is the same either way (the in-SM sort
  *                orders (key, position) pairs).
- *   max_levels   partition levels of rsort_sort / rsort_segmented before
- *                every bucket is final (1..3, default 3).  A bucket still
- *                above 4096 keys after the last level is merge-sorted
- *                through global memory by one CTA (slow; with 3 levels the
- *                sampling makes it vanishingly rare below 2^31 keys).
+ *   max_levels   at most this many partition levels of rsort_sort /
+ *                rsort_segmented (1..3, default 3); a call launches fewer
+ *                when its sizes bound every bucket within 4096 keys sooner
+ *                (n / p, the fan-out targets and the 512-bucket cap of a
+ *                deeper level: 2^28 keys at p = 1024 take two).  A bucket
+ *                still above 4096 keys after the last level is merge-sorted
+ *                through global memory by one CTA (slow; rare).
  *   The in-SM sort of a bucket is chosen by its size (Section 6's
  *   size-dependent choice, applied per bucket; paper_1606_08766_gb300.autotune
  *   measures these on the device and writes a table of them):

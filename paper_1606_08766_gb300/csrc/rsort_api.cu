@@ -157,6 +157,32 @@ void layout(Plan& p) {
 void plan_levels(Plan& p, uint64_t n, uint32_t k1, uint64_t g1, int num_sms, int levels) {
   p.n = n;
   p.k1 = k1;
+  // Levels the sizes call for (at most the max_levels tunable): the sample
+  // keeps a level's largest bucket within ~1.5x its mean, so a level-1
+  // bucket holds up to 1.5 n / k1 keys (an automatic fan-out aims at the
+  // target, at most kMaxKDeep buckets per segment), and a level-2 bucket up
+  // to 1.5x the target while level 2's fan-out stays below kMaxKDeep.  Where
+  // those bounds keep the buckets within kBucketCap a further level would
+  // find nothing to do (its launches cost ~0.1 ms); a bucket that still
+  // exceeds kBucketCap after the last level goes to the oversize merge, so
+  // the choice changes speed only.
+  {
+    uint64_t tmin = p.target_bucket, tmax = p.target_bucket;
+    for (int c = 0; c <= 32; ++c)
+      if (p.target_by_class[c]) {
+        tmin = std::min<uint64_t>(tmin, p.target_by_class[c]);
+        tmax = std::max<uint64_t>(tmax, p.target_by_class[c]);
+      }
+    const uint64_t mean1 =
+        k1 >= 2 ? n / k1 : std::max<uint64_t>(n / (uint64_t)kMaxKDeep, tmax);
+    int needed = 3;
+    if (3 * mean1 <= 2 * (uint64_t)kBucketCap)
+      needed = 1;
+    else if (3 * tmax <= 2 * (uint64_t)kBucketCap &&
+             3 * mean1 <= 2 * (uint64_t)kMaxKDeep * tmin)
+      needed = 2;
+    levels = std::min(levels, needed);
+  }
   p.levels = levels;
   // level 1 of one segment: 6 chunks per SM, so grids of 1, 2, 3 or 6 resident
   // CTAs per SM all get the same number of chunks

@@ -365,3 +365,31 @@ def test_sort_replayed_from_cuda_graph(oracle_mod, name):
         np.testing.assert_array_equal(_host_u32(po), rp)
         np.testing.assert_array_equal(_host_u64(ko), rk)
         c.check()
+
+
+@pytest.mark.parametrize("p", [64, 1024])
+def test_unaligned_buffers(ctx, oracle_mod, p):
+    # keys, sorted keys and permutation one element into their allocations:
+    # the key arrays are 8-byte but not 16-byte aligned (the classify falls
+    # back to checked 8-byte loads) and the output units start mid-line
+    n = (1 << 18) + 5
+    keys = instances.generate("uniform", n, p=p, seed=12)
+    store = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    store[1:].copy_(_dev(keys))
+    x = store[1:]
+    assert x.data_ptr() % 16 == 8
+    ko_store = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    po_store = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    ko, po = ko_store[1:], po_store[1:]
+    ctx.sort(x, p=p, seed=2, keys_out=ko, perm_out=po)
+    torch.cuda.synchronize()
+    rk, rp = oracle_mod.sort(keys)
+    np.testing.assert_array_equal(_host_u32(po), rp)
+    np.testing.assert_array_equal(_host_u64(ko), rk)
+    k = min(p, 256)
+    ref = oracle_mod.partition(keys, k, seed=5)
+    pk, pp, off = ctx.partition(x, k, seed=5)
+    np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), ref["offsets"])
+    np.testing.assert_array_equal(_host_u32(pp), ref["pos_out"])
+    np.testing.assert_array_equal(_host_u64(pk), ref["keys_out"])
+    ctx.check()
