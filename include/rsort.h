@@ -341,7 +341,8 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *   small_cap, mid_cap  buckets of at most small_cap keys (64..1024, default
  *                1024) are sorted by 128-thread CTAs of 8 slots a thread, of
  *                at most mid_cap (64..2048, default 2048) by 128-thread CTAs
- *                of 16 slots, larger ones (up to 4096) by 512-thread CTAs.
+ *                of 16 slots, larger ones (up to 4096) by 256-thread CTAs of
+ *                16 slots.
  *   rank_max     buckets of at most this many keys (0..128, default 64) are
  *                sorted by rank-by-counting (Appendix "Fast Work-Inefficient
  *                Ranking").

@@ -13,7 +13,7 @@ the device instead of fixing it by hand:
   (``sort_small``), bins, quicksort or bitonic for the mid and medium classes
   (``sort_mid``, ``sort_medium``), and the class cut-offs that pick the CTA
   shape (``small_cap``: 128 threads of 8 slots up to it, ``mid_cap``: 128
-  threads of 16 slots up to it, 512-thread CTAs above);
+  threads of 16 slots up to it, 256 threads of 16 slots above);
 * the sample-sort fan-out of a segment, per segment-size class
   c = ceil(log2 m): the bucket size it aims at (``target_bucket@c``, i.e. the
   bucket count k = ceil(m / target)).
