@@ -52,11 +52,13 @@ ALGO_BYTES_PER_KEY = {
 # grows in proportion to the keys; the capture and command are summarised in
 # profiles/).  Remove an entry whenever its kernel changes.
 MEASURED_TRAFFIC_PER_KEY = {
-    "L1.scatter": 23.66,       # 0.7693 + 0.8185 GB at 2^26 keys (k_scatter_units<512,12,0,0>)
+    "L1.scatter": 23.64,       # 0.7696 + 0.8171 GB at 2^26 keys (k_scatter_units<512,12,0,0>)
     "L1.classify": 9.50,       # 0.5473 + 0.0897 GB (k_classify_ids, ids included)
-    "L2.scatter": 25.35,       # 0.9511 + 0.7504 GB (k_scatter_units<512,12,1,0>)
-    "L2.classify": 9.38,       # 0.5518 + 0.0780 GB (k_classify_count<2>)
-    "local_sort_mid": 23.09,   # 0.6684 + 0.6133 GB over 55.5 M keys of the class
+    "L2.scatter": 25.35,       # 0.9512 + 0.7498 GB (k_scatter_units<512,12,1,0>)
+    "L2.classify": 9.39,       # 0.5517 + 0.0787 GB (k_classify_count<2>)
+    "local_sort_mid": 23.15,   # 0.6691 + 0.6138 GB over 55.4 M keys of the class
+    "local_sort_medium": 18.42,  # 0.1037 + 0.0548 GB over 8.6 M keys (writes left in L2)
+    "local_sort": 13.08,       # 0.0379 + 0.0025 GB over 3.1 M keys (writes left in L2)
 }
 
 
