@@ -421,14 +421,20 @@ def batched_leg(ctx, tuned, dev, nseg, maxlog, total_cap=None, plain_max=20_000,
             "identical_to_plain": same}
 
 
-def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95, 1.2),
-                budget=64 << 30, seed=5):
+def serving_leg(dev, requests=1000, slots=1000, lo_log2=4, hi_log2=26,
+                loads=(0.5, 0.8, 0.95, 1.2), budget=64 << 30, seed=5):
     """Config 5: a stream of sort requests with sizes log-uniform in
     [2^lo, 2^hi], u64 or f64 keys (50/50), each drawing one of the 11
     instances, p_virtual = min(1024, ceil(n / 2^8)), served by continuous
     batching under an HBM budget, against serial plain sorts of the same
     requests.  Capacity = everything offered at once; then Poisson arrivals
-    at the given fractions of that capacity, each with p50 / p99 latency."""
+    at the given fractions of that capacity, each with p50 / p99 latency.
+
+    The requests' device buffers stay resident: min(requests, slots) distinct
+    requests are drawn, and arrival i reuses the buffers of request
+    i mod slots, once the arrival that used them before has finished (an
+    arrival that has to wait for that is counted as blocked: the stream is
+    then no longer open-loop for it)."""
     import math
     import random
 
@@ -438,8 +444,9 @@ def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95
     from paper_1606_08766_gb300 import Context
 
     rng = random.Random(seed)
+    nslots = min(requests, slots)
     sizes = [int(math.exp(rng.uniform(lo_log2 * math.log(2), hi_log2 * math.log(2))))
-             for _ in range(requests)]
+             for _ in range(nslots)]
     reqs = []
     for i, n in enumerate(sizes):
         name = instances.NAMES[rng.randrange(len(instances.NAMES))]
@@ -453,6 +460,7 @@ def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95
     total = sum(sizes)
     torch.cuda.synchronize(dev)
     ctx = Context(dev.index, hbm_budget_bytes=budget)
+    assert requests <= ctx.get_tunable("serve_history"), "every ticket must stay readable"
 
     def offer_all():
         t0 = time.perf_counter()
@@ -479,13 +487,14 @@ def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95
     torch.cuda.synchronize(dev)
     wall_plain = time.perf_counter() - t0
     plain.close()
-    cap_rate = requests / wall
-    out = {"workload": f"{requests} requests (of the 200,000 of the stated stream), sizes "
+    cap_rate = nslots / wall
+    out = {"workload": f"{requests} requests (of the 200,000 of the stated stream) cycling "
+                       f"through {nslots} distinct resident requests, sizes "
                        f"log-uniform in [2^{lo_log2}, 2^{hi_log2}], u64/f64 50/50, a random "
-                       f"instance each, p_virtual = min(1024, ceil(n/2^8)), {total} keys, "
-                       f"HBM budget {budget >> 30} GiB",
+                       f"instance each, p_virtual = min(1024, ceil(n/2^8)), {total} keys "
+                       f"in the distinct requests, HBM budget {budget >> 30} GiB",
            "capacity_requests_s": cap_rate, "served_gkeys_s": total / wall / 1e9,
-           "plain_serial_requests_s": requests / wall_plain,
+           "plain_serial_requests_s": nslots / wall_plain,
            "plain_serial_gkeys_s": total / wall_plain / 1e9,
            "speedup_vs_plain": wall_plain / wall,
            "saturated_p50_us": sat["p50_us"], "saturated_p99_us": sat["p99_us"],
@@ -494,20 +503,30 @@ def serving_leg(dev, requests=1000, lo_log2=4, hi_log2=26, loads=(0.5, 0.8, 0.95
         rate = load * cap_rate
         ctx.reset_serve_stats()
         ts = []
+        blocked = 0
+        keys_served = 0
         t_start = time.perf_counter()
         t_next = t_start
-        for t, o, pm, kt, p in reqs:
+        for i in range(requests):
             t_next += rng.expovariate(rate)
             while time.perf_counter() < t_next:
                 pass
+            t, o, pm, kt, p = reqs[i % nslots]
+            if i >= nslots:  # this request's buffers: their previous user must be done
+                prev = ts[i - nslots]
+                blocked += ctx.poll(prev)[0] == 1
+                assert ctx.wait(prev, 300) == 0
             ts.append(ctx.submit(t, o, pm, p=p, key_type=kt))
-        for t in ts:
+            keys_served += t.numel()
+        for t in ts[max(0, requests - nslots):]:
             assert ctx.wait(t, 300) == 0
         el = time.perf_counter() - t_start
         st = ctx.serve_stats()
+        assert st["completed"] == requests
         out["loads"][str(load)] = {"offered_requests_s": rate, "served_requests_s": requests / el,
-                                   "served_gkeys_s": total / el / 1e9, "p50_us": st["p50_us"],
-                                   "p99_us": st["p99_us"], "max_us": st["max_us"]}
+                                   "served_gkeys_s": keys_served / el / 1e9, "p50_us": st["p50_us"],
+                                   "p99_us": st["p99_us"], "max_us": st["max_us"],
+                                   "blocked_arrivals": blocked}
     ctx.close()
     del reqs
     torch.cuda.empty_cache()
@@ -715,7 +734,7 @@ def run_rsort(args):
                               label="config 4b: ")}
         tuned.close()
         torch.cuda.empty_cache()
-        extra["serving"] = serving_leg(dev)
+        extra["serving"] = serving_leg(dev, requests=args.serving_requests)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
@@ -746,6 +765,9 @@ def main():
                     help="skip the batched-segmented and serving legs")
     ap.add_argument("--tunable", action="append", default=[],
                     help="name=value tunable of the library context (repeatable)")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="arrivals of the serving leg (the stated stream has 200,000; "
+                         "its buffers cycle through at most 1,000 resident requests)")
     ap.add_argument("--n", type=int, default=N_KEYS,
                     help="keys per GPU (default 2^28; smaller values are for profiling)")
     args = ap.parse_args()

@@ -250,6 +250,11 @@ rsort_status rsort_partition_noalloc(rsort_key_type type, const void *d_keys_in,
  * The caller owns the request's device buffers; they must stay valid and
  * untouched until the ticket reports a final status.  p_virtual only matters
  * for requests that run alone (it does not change results).
+ *
+ * The runtime keeps the final status and latency of the last `serve_history`
+ * finished requests (default 2^20); an older ticket is forgotten and then
+ * reads as unknown (EINVAL), so a long-running server holds bounded host
+ * memory.
  * ------------------------------------------------------------------------- */
 typedef struct {
     rsort_key_type type;
@@ -268,11 +273,13 @@ rsort_status rsort_submit(rsort_ctx *ctx, const rsort_request *req, uint64_t *ti
 
 /* Non-blocking status: RSORT_PENDING (queued or running), RSORT_OK (done;
  * *latency_ns_out, if not NULL, gets submit-to-completion nanoseconds),
- * RSORT_ECANCELLED, or the request's error.  EINVAL for an unknown ticket. */
+ * RSORT_ECANCELLED, or the request's error.  EINVAL for an unknown ticket
+ * (never issued, or finished more than `serve_history` requests ago). */
 rsort_status rsort_poll(rsort_ctx *ctx, uint64_t ticket, uint64_t *latency_ns_out);
 
 /* Blocks until the request has a final status or timeout_ns passes
- * (RSORT_ETIMEOUT).  Returns the final status otherwise. */
+ * (RSORT_ETIMEOUT).  Returns the final status otherwise, or EINVAL if the
+ * ticket is unknown (as for rsort_poll). */
 rsort_status rsort_wait(rsort_ctx *ctx, uint64_t ticket, uint64_t timeout_ns);
 
 /* Cancels a request that has not started: RSORT_OK, its buffers are left
@@ -290,8 +297,9 @@ typedef struct {
     double elapsed_s;                /* first submit to last completion */
 } rsort_serve_stats;
 
-/* Counters and latency percentiles since the runtime started (or the last
- * reset).  All zero before the first submit. */
+/* Counters since the runtime started (or the last reset), and latency
+ * percentiles over the last `serve_history` completions in that time.  All
+ * zero before the first submit. */
 rsort_status rsort_get_serve_stats(rsort_ctx *ctx, rsort_serve_stats *out);
 rsort_status rsort_reset_serve_stats(rsort_ctx *ctx);
 
@@ -311,8 +319,9 @@ rsort_status rsort_phase_times(rsort_ctx *ctx, const char **names, double *ms,
  *                1 (default): a lookup table over the keys' leading bits
  *                into the same sorted splitters, then a binary search inside
  *                the bin.
- *   serve_slots, serve_batch_keys, serve_alone_min  serving runtime (see
- *                rsort_submit); fixed once the runtime has started.
+ *   serve_slots, serve_batch_keys, serve_alone_min, serve_history
+ *                serving runtime (see rsort_submit); fixed once the runtime
+ *                has started.
  *   target_bucket  automatic fan-outs aim at final buckets of this many keys
  *                (64..4096, default 1536).
  *   level1_stable  level 1 of rsort_sort / rsort_segmented: 1 keeps input

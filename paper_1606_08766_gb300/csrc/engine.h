@@ -108,6 +108,7 @@ struct rsort_ctx {
   int serve_slots = 4;                    // batches in flight (streams)
   uint64_t serve_batch_keys = 1ull << 24; // keys per batch
   uint64_t serve_alone_min = 1ull << 20;  // larger requests run as a batch of their own
+  uint64_t serve_history = 1ull << 20;    // finished requests whose status (and latency) is kept
 };
 
 namespace rsort {

@@ -430,6 +430,11 @@ rsort_status set_tunable(rsort_ctx* c, const char* name, long long v) {
     c->serve_alone_min = (uint64_t)v;
     return RSORT_OK;
   }
+  if (strcmp(name, "serve_history") == 0) {
+    if (v < 1 || v > (1ll << 26)) return RSORT_EINVAL;
+    c->serve_history = (uint64_t)v;
+    return RSORT_OK;
+  }
   return RSORT_EINVAL;
 }
 
@@ -1028,6 +1033,10 @@ rsort_status rsort_get_tunable(rsort_ctx* c, const char* name, int64_t* value) {
   }
   if (strcmp(name, "serve_alone_min") == 0) {
     *value = (int64_t)c->serve_alone_min;
+    return RSORT_OK;
+  }
+  if (strcmp(name, "serve_history") == 0) {
+    *value = (int64_t)c->serve_history;
     return RSORT_OK;
   }
   return RSORT_EINVAL;

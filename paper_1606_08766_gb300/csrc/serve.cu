@@ -19,6 +19,9 @@
 // stamps each request's latency.  Results never depend on the batch a request
 // lands in: every request is sorted as its own segment, and the output of the
 // robust sort is unique.
+// The runtime keeps the record (status, latency) of the last `serve_history`
+// finished requests and forgets older ones, so a server that runs for
+// millions of requests holds bounded host memory.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -126,12 +129,15 @@ struct Server {
   std::condition_variable done_cv;  // wakes waiters
   std::deque<uint64_t> queue;
   std::unordered_map<uint64_t, Req> reqs;
+  uint64_t history = 1ull << 20;  // finished requests whose record is kept
+  std::deque<uint64_t> finished;  // their tickets, oldest first
   Slot slots[kMaxSlots];
   std::thread th;
   bool stop = false;
   uint64_t next_ticket = 1;
   // statistics
-  std::vector<double> lat_ns;
+  std::vector<double> lat_ns;  // latencies of the last `history` completions (a ring)
+  size_t lat_next = 0;         // ring slot the next latency overwrites once full
   uint64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, batches = 0;
   uint64_t batched_requests = 0, keys_done = 0;
   bool have_first = false;
@@ -145,6 +151,25 @@ struct Server {
   static void CUDART_CB on_done(void* p) {
     CbArg* a = static_cast<CbArg*>(p);
     a->s->finish_slot(a->slot);
+  }
+
+  // A request reached a final state and left the queue (lock held): it joins
+  // the finished records, and the oldest record beyond `history` is dropped.
+  void retire(uint64_t t) {
+    finished.push_back(t);
+    while (finished.size() > history) {
+      reqs.erase(finished.front());
+      finished.pop_front();
+    }
+  }
+
+  void record_latency(double ns) {
+    if (lat_ns.size() < history) {
+      lat_ns.push_back(ns);
+    } else {
+      lat_ns[lat_next] = ns;
+      lat_next = (lat_next + 1) % history;
+    }
   }
 
   // Called from the CUDA callback thread: no CUDA calls here.
@@ -165,9 +190,10 @@ struct Server {
         q.status = RSORT_OK;
         ++completed;
         keys_done += q.r.n;
-        lat_ns.push_back(
+        record_latency(
             (double)std::chrono::duration_cast<std::chrono::nanoseconds>(now - q.t_submit).count());
       }
+      retire(t);
     }
     t_last = now;
     sl.tickets.clear();
@@ -193,12 +219,22 @@ struct Server {
     return segmented_scratch_bytes(c, keys, nreq) + batch_layout(keys, nreq).total;
   }
 
+  // Whether ticket t is waiting in the queue (lock held); a cancelled entry
+  // that leaves the queue here is retired.
+  bool still_queued(uint64_t t) {
+    const auto it = reqs.find(t);
+    if (it == reqs.end()) return false;
+    if (it->second.state == RState::Queued) return true;
+    retire(t);
+    return false;
+  }
+
   // Forms the next batch from the queue front (lock held).  Returns false if
   // the queue holds only cancelled entries.
   bool form_batch(std::vector<uint64_t>& out, bool& alone, uint64_t& keys) {
     out.clear();
     keys = 0;
-    while (!queue.empty() && reqs[queue.front()].state != RState::Queued) queue.pop_front();
+    while (!queue.empty() && !still_queued(queue.front())) queue.pop_front();
     if (queue.empty()) return false;
     const uint64_t first = queue.front();
     const Req& f = reqs[first];
@@ -211,8 +247,8 @@ struct Server {
     }
     std::deque<uint64_t> rest;
     for (uint64_t t : queue) {
+      if (!still_queued(t)) continue;
       const Req& q = reqs[t];
-      if (q.state != RState::Queued) continue;
       const bool fits = q.r.type == f.r.type && q.r.n <= alone_min &&
                         keys + q.r.n <= batch_keys && out.size() < kMaxBatchRequests;
       if (fits || out.empty()) {
@@ -290,6 +326,7 @@ struct Server {
       q.status = s;
       q.t_done = now;
       ++failed;
+      retire(t);
     }
     done_cv.notify_all();
   }
@@ -373,6 +410,7 @@ rsort::Server* get_server(rsort_ctx* c, rsort_status* err) {
   s->nslots = std::max(1, std::min(kMaxSlots, c->serve_slots));
   s->batch_keys = c->serve_batch_keys;
   s->alone_min = c->serve_alone_min;
+  s->history = std::max<uint64_t>(1, c->serve_history);
   bool ok = true;
   for (int i = 0; i < s->nslots && ok; ++i) {
     Slot& sl = s->slots[i];
@@ -491,6 +529,7 @@ rsort_status rsort_submit(rsort_ctx* c, const rsort_request* r, uint64_t* ticket
     q.t_done = q.t_submit;
     ++s->completed;
     s->reqs[t] = q;
+    s->retire(t);
   } else {
     s->reqs[t] = q;
     s->queue.push_back(t);
@@ -518,11 +557,16 @@ rsort_status rsort_wait(rsort_ctx* c, uint64_t ticket, uint64_t timeout_ns) {
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return RSORT_EINVAL;
   const auto deadline = Clock::now() + std::chrono::nanoseconds(timeout_ns);
+  // the record may be dropped while this thread sleeps (more than
+  // serve_history later requests finished): the ticket is then unknown
   const bool done = s->done_cv.wait_until(lk, deadline, [&] {
-    return terminal(s->reqs[ticket].state);
+    const auto i = s->reqs.find(ticket);
+    return i == s->reqs.end() || terminal(i->second.state);
   });
   if (!done) return RSORT_ETIMEOUT;
-  return report(s->reqs[ticket], nullptr);
+  const auto i = s->reqs.find(ticket);
+  if (i == s->reqs.end()) return RSORT_EINVAL;
+  return report(i->second, nullptr);
 }
 
 rsort_status rsort_cancel(rsort_ctx* c, uint64_t ticket) {
@@ -554,8 +598,10 @@ rsort_status rsort_get_serve_stats(rsort_ctx* c, rsort_serve_stats* out) {
     out->completed = s->completed;
     out->cancelled = s->cancelled;
     out->failed = s->failed;
-    for (uint64_t t : s->queue)
-      if (s->reqs[t].state == RState::Queued) ++out->queued;
+    for (uint64_t t : s->queue) {
+      const auto i = s->reqs.find(t);
+      if (i != s->reqs.end() && i->second.state == RState::Queued) ++out->queued;
+    }
     out->inflight_batches = (uint32_t)s->busy_slots();
     out->batches = s->batches;
     out->keys_completed = s->keys_done;
@@ -576,6 +622,7 @@ rsort_status rsort_reset_serve_stats(rsort_ctx* c) {
   if (!s) return RSORT_OK;
   std::lock_guard<std::mutex> lk(s->mu);
   s->lat_ns.clear();
+  s->lat_next = 0;
   s->submitted = s->completed = s->cancelled = s->failed = s->batches = 0;
   s->batched_requests = s->keys_done = 0;
   s->have_first = false;

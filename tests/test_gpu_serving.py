@@ -123,3 +123,41 @@ def test_budget_admission_and_bounded_wait():
         k1, p1 = ctx.sort(keys, p=1)
         assert torch.equal(k1, ko) and torch.equal(p1, po)
         assert ctx.poll(123456789)[0] == EINVAL
+
+
+def test_finished_records_are_bounded_by_serve_history():
+    """Only the last serve_history finished requests keep their record: an
+    older ticket reads as unknown, the newer ones keep status and latency,
+    the latency percentiles cover the kept completions, and every result is
+    still the sort of that request alone."""
+    from paper_1606_08766_gb300 import Context, RsortError
+    with Context(0) as ctx:
+        assert ctx.get_tunable("serve_history") == 1 << 20
+        ctx.set_tunable("serve_history", 4)
+        keys = [torch.from_numpy(instances.generate("uniform", 3000 + 17 * s, seed=s)
+                                 .view(np.int64)).cuda() for s in range(10)]
+        outs = [(torch.empty_like(k), torch.empty(k.numel(), dtype=torch.int32, device="cuda"))
+                for k in keys]
+        torch.cuda.synchronize()
+        tickets = []
+        for k, (o, p) in zip(keys, outs):
+            tickets.append(ctx.submit(k, o, p))
+            assert ctx.wait(tickets[-1], timeout_s=120) == OK  # one finishes before the next
+        for t in tickets[:6]:
+            assert ctx.poll(t)[0] == EINVAL and ctx.wait(t, timeout_s=1) == EINVAL
+        for t in tickets[6:]:
+            st, lat = ctx.poll(t)
+            assert st == OK and lat > 0
+        stats = ctx.serve_stats()
+        assert stats["completed"] == 10 and stats["failed"] == 0
+        assert stats["p99_us"] >= stats["p50_us"] > 0
+        # n = 0 finishes at submit and counts as a finished request too
+        empty = torch.empty(0, dtype=torch.int64, device="cuda")
+        t0 = ctx.submit(empty, torch.empty_like(empty),
+                        torch.empty(0, dtype=torch.int32, device="cuda"))
+        assert ctx.poll(t0)[0] == OK and ctx.poll(tickets[6])[0] == EINVAL
+        with pytest.raises(RsortError):
+            ctx.set_tunable("serve_history", 8)  # fixed once the runtime has started
+        for k, (o, p) in zip(keys, outs):
+            k1, p1 = ctx.sort(k, p=1)
+            assert torch.equal(k1, o) and torch.equal(p1, p)
