@@ -217,7 +217,7 @@ rsort_status rsort_segmented(rsort_ctx *ctx, rsort_key_type type, const void *d_
  *     every GPU loading the library holds until the process exits.  Limit:
  *     k <= 1024 (any n <= 2^32 - 1); larger k returns RSORT_EINVAL.
  *   - The first call on a device looks up that array's device address and
- *     sets kernel attributes; make that first call before any stream capture.
+ *     sets kernel attributes (runtime calls that later calls skip).
  *   - Every call uses the same array (its contents persist between calls and
  *     are re-initialised by each call), so calls whose work overlaps on the
  *     GPU (other streams, other host threads) race: serialise them.
