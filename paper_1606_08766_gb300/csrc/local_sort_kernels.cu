@@ -12,7 +12,7 @@
 //
 // The sorted buckets come in three size classes, each its own kernel with a
 // CTA shape that fits it: <= 1024 keys (128 threads, 10 CTAs per SM),
-// <= 2048 keys (128 threads, 5 per SM), <= 4096 keys (512 threads, 2 per SM).
+// <= 2048 keys (128 threads, 5 per SM), <= 4096 keys (256 threads, 2 per SM).
 // Buckets are taken from a device work list with an atomic cursor by a
 // persistent grid.  The final store restores float64 bit patterns.
 #include "cta_quicksort.cuh"
