@@ -8,11 +8,12 @@
 //   m <= kRankMax       rank-by-counting: slot = #{pairs smaller than me}
 //                       (the ranking of Appendix "Fast Work-Inefficient
 //                       Ranking", all in one CTA)
-//   otherwise           split the bucket's key range [min, max] into ~2m
-//                       equal-width bins (a counting sort in shared memory),
-//                       then rank by counting inside each bin (an element
-//                       alone in its bin is already in place); the bins of a
-//                       bucket are tiny unless its keys cluster
+//   otherwise           split the bucket's key range [min, max] into
+//                       2 * next_pow2(m) equal-width bins (a counting sort in
+//                       shared memory), then order each bin that holds
+//                       several elements by insertion (an element alone in
+//                       its bin is already in place); the bins of a bucket
+//                       are tiny unless its keys cluster
 //   a crowded bin       bitonic sort of the whole bucket (Appendix "Bitonic
 //   (> kBinLimit)       Sort"), which needs no assumption on the keys
 //
